@@ -1,0 +1,172 @@
+/*
+ * scion.h — C ABI of the GB300 (sm_103a) closest-hit / any-hit traversal
+ * library for triangle BVHs whose physical data layout is chosen separately
+ * from one traversal loop.
+ *
+ * The calls follow the paper's statement of the problem (Section 3, Fig. 4 and
+ * App. G "Closest Hit Ray Tracing": a Ray, a logical BVH over triangles, and
+ * the closest_hit query) and its decoupling of physical layout from traversal
+ * (Section 4, the layout language; Section 5, two-phase build; Table 1, the
+ * evaluated layouts).
+ *
+ * General conventions
+ *  - Every call returns a scion_status; no call aborts, traps or throws.
+ *  - Argument and descriptor errors are reported synchronously and nothing is
+ *    launched.
+ *  - Trace calls are asynchronous on the given stream. They never synchronise
+ *    the host. Errors found on the device (stack overflow, step limit) are
+ *    recorded in the BVH's device status word and the affected ray's hit gets
+ *    prim = SCION_PRIM_ERROR; scion_get_status reads and clears that word.
+ *  - Device pointers are CUDA device addresses on the current device.
+ *  - Rays and hits are caller-owned. The BVH owns its own device buffers.
+ *  - One BVH may be traced by several calls in a row on one stream. Calls on
+ *    the same BVH issued concurrently on different streams share its device
+ *    work counter and race: order them on one stream.
+ */
+#ifndef SCION_H
+#define SCION_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *scion_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  SCION_OK = 0,
+  SCION_ERR_INVALID_ARG = 1,
+  SCION_ERR_UNSUPPORTED_LAYOUT = 2,
+  SCION_ERR_OOM = 3,
+  SCION_ERR_CUDA = 4,
+  SCION_ERR_STACK_OVERFLOW = 5,
+  SCION_ERR_ITER_LIMIT = 6,
+  SCION_ERR_BAD_INPUT = 7
+} scion_status;
+
+#define SCION_PRIM_MISS 0xFFFFFFFFu
+#define SCION_PRIM_ERROR 0xFFFFFFFEu
+
+/* Layout descriptor: the physical representation of one logical BVH
+ * (Section 4 layout primitives: node arity, group AoS/SoA (Section 4.2.2),
+ * quantised derived bounds (Section 4.2.1, App. D.2), bit-stolen or indirect
+ * references (split / indirect group ... from, Section 4.2.2-4.2.3), and the
+ * build order attribute order=pre (Section 5.3.2)).
+ *
+ *  width      : 2, 4 or 8 children per node.
+ *  box_layout : 0 AoS, 1 SoA. For width 2 with f32 boxes the node stores its
+ *               own box (the PBRTv4 LinearBVH of Fig. 4b, 32 B per node);
+ *               SoA then splits boxes and references into two arrays. For all
+ *               other layouts child boxes are stored in the parent node,
+ *               interleaved per child (AoS) or per coordinate (SoA).
+ *  box_prec   : 0 f32, 1 f16 (world frame, rounded outward),
+ *               2 u8 (relative to the parent's merged box, rounded outward,
+ *               App. D.2 reading). f16/u8 need a children-in-parent node.
+ *  child_ref  : 0 direct (an explicit reference per child; for the width-2
+ *               own-box node: implicit left = I+1 and stored right offset,
+ *               which requires order = DFS), 1 indirect (one base index,
+ *               siblings stored contiguously).
+ *  prim_ref   : 0 direct (triangles copied in leaf order, 48 B each),
+ *               1 indirect (a 32-bit triangle id per leaf entry into the BVH's
+ *               vertex/index tables).
+ *  order      : 0 DFS pre-order, 1 BFS, 2 treelet (greedy, surface-area
+ *               ordered clusters of at most treelet_bytes).
+ *  leaf_max   : triangles per leaf, 1..16 (0 = 4).
+ *  sah_bins   : SAH bins, 2..64 (0 = 16).
+ *  treelet_bytes : treelet budget in bytes (0 = 1024).
+ *  reserved   : must be 0.
+ * Unsupported combinations return SCION_ERR_UNSUPPORTED_LAYOUT. */
+typedef struct {
+  uint32_t width;
+  uint32_t box_layout;
+  uint32_t box_prec;
+  uint32_t child_ref;
+  uint32_t prim_ref;
+  uint32_t order;
+  uint32_t leaf_max;
+  uint32_t sah_bins;
+  uint32_t treelet_bytes;
+  uint32_t reserved;
+} scion_layout_desc;
+
+/* A ray (the paper's Ray of Fig. 4 with an added tmin): accepted hits satisfy
+ * tmin <= t <= tmax. 32 bytes, 16-byte aligned arrays. */
+typedef struct {
+  float ox, oy, oz, tmin;
+  float dx, dy, dz, tmax;
+} scion_ray;
+
+/* A closest hit: t, barycentric weights u (of p1) and v (of p2), and the
+ * caller's triangle index. A miss is t = +inf, u = v = 0,
+ * prim = SCION_PRIM_MISS. 16 bytes. */
+typedef struct {
+  float t, u, v;
+  uint32_t prim;
+} scion_hit;
+
+/* Traversal parameters; NULL or 0 fields = defaults.
+ *  threads_per_block : CTA size (multiple of 32, <= 1024; default 256).
+ *  ctas_per_sm       : persistent CTAs per SM (default: from occupancy).
+ *  reg_stack         : reserved (0).
+ *  smem_stack        : shared-memory stack entries per thread (default 16).
+ *  ordered_children  : 0 or 1 = visit nearer children first (closest-hit),
+ *                      2 = stored slot order.
+ *  rays_per_fetch    : reserved (0).
+ *  max_steps         : per-ray node+leaf visit limit (0 = derived from size).
+ *  reserved          : must be 0. */
+typedef struct {
+  uint32_t threads_per_block, ctas_per_sm, reg_stack, smem_stack, ordered_children,
+      rays_per_fetch, max_steps, reserved;
+} scion_trace_params;
+
+typedef struct scion_bvh_s *scion_bvh;
+
+/* Build a BVH (Section 5.1 two-phase construction: binned-SAH logical BVH2,
+ * Section 9.1; collapse to the requested width; order; count pass, one
+ * allocation per buffer, fill pass, App. F) and upload it.
+ *  verts   : float [n_verts][3], host or device memory (read, not retained).
+ *  indices : uint32 [n_tris][3] or NULL for a soup (triangle i = vertices
+ *            3i..3i+2, n_verts must be 3*n_tris). Host or device memory.
+ *  desc    : layout descriptor (host).
+ *  stream  : stream for the uploads; the call returns after they complete.
+ *  out     : receives the handle; *out is NULL on error.
+ * Triangles with a non-finite vertex are never hit and are left out.
+ * Errors: INVALID_ARG (null pointers, index out of range, n_tris >= 2^27),
+ * UNSUPPORTED_LAYOUT, OOM, CUDA. */
+scion_status scion_build(const float *verts, uint64_t n_verts, const uint32_t *indices,
+                         uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
+                         scion_bvh *out);
+
+/* Sizes of the device buffers (bytes) and tree shape. Any output pointer may
+ * be NULL. node_bytes: node buffer(s); prim_bytes: leaf primitive buffer
+ * (direct triangles, or ids plus the index table for indirect); depth: levels
+ * of the stored tree; n_nodes: stored nodes. */
+scion_status scion_bvh_info(scion_bvh bvh, uint64_t *node_bytes, uint64_t *prim_bytes,
+                            uint32_t *depth, uint32_t *n_nodes);
+
+/* Closest hit of each ray (Fig. 4 closest_hit; ties at equal t go to the
+ * lowest triangle index). d_rays: device scion_ray[n]; d_hits: device
+ * scion_hit[n]. params: NULL for defaults. n = 0 is a no-op. */
+scion_status scion_trace_closest(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
+                                 scion_hit *d_hits, const scion_trace_params *params,
+                                 scion_stream stream);
+
+/* Any hit: d_occluded[i] = 1 iff ray i has an accepted hit in [tmin, tmax],
+ * else 0 (device uint32[n]). */
+scion_status scion_trace_any(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
+                             uint32_t *d_occluded, const scion_trace_params *params,
+                             scion_stream stream);
+
+/* Device status of the BVH since the last call: synchronises the stream,
+ * returns SCION_OK or the first device-side error code, and clears it. */
+scion_status scion_get_status(scion_bvh bvh, scion_stream stream, scion_status *device_status);
+
+void scion_destroy(scion_bvh bvh);
+
+const char *scion_status_string(scion_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

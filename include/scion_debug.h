@@ -1,0 +1,75 @@
+/*
+ * scion_debug.h — introspection entry points of the scion library, used by
+ * the test suite to check the packer and the codecs without a GPU.
+ *
+ * The paper's round-trip property (App. B, "Round-Trip Soundness": decoding
+ * an encoded tree gives back the logical tree) is checked through these
+ * calls: a host-only build packs a scene exactly as scion_build does, and the
+ * decode call reads every packed node back into its logical view (child
+ * kind, child node or leaf range, conservative box).
+ *
+ * All pointers here are host memory owned by the caller. None of these calls
+ * touches a GPU.
+ */
+#ifndef SCION_DEBUG_H
+#define SCION_DEBUG_H
+
+#include <stdint.h>
+
+#include "scion.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scion_host_bvh_s *scion_host_bvh;
+
+typedef struct {
+  uint32_t n_nodes;        /* stored nodes */
+  uint32_t node_stride;    /* bytes per node in the (first) node array */
+  uint32_t n_leaf_entries; /* triangles referenced by leaves */
+  uint32_t root_ref;       /* encoded root reference (wide) or 0 (own-box) */
+  uint32_t depth;          /* levels of the stored tree */
+  uint32_t stack_need;     /* worst-case traversal stack entries */
+  uint32_t own_box;        /* 1 = width-2 own-box node */
+  uint32_t reserved;
+  uint64_t node_bytes;     /* node buffer(s) */
+  uint64_t prim_bytes;     /* leaf primitive buffer (+ index table if indirect) */
+  uint64_t vert_bytes;     /* float4 vertex table */
+  double build_ms;         /* host build + pack time */
+} scion_debug_info;
+
+/* Build and pack on the host only (same code path as scion_build, no upload).
+ * verts/indices: host arrays as in scion_build. Errors as scion_build. */
+scion_status scion_debug_build_host(const float *verts, uint64_t n_verts, const uint32_t *indices,
+                                    uint64_t n_tris, const scion_layout_desc *desc,
+                                    scion_host_bvh *out);
+
+scion_status scion_debug_host_stats(scion_host_bvh hb, scion_debug_info *info);
+
+/* Decode every packed node. Arrays sized for n_nodes * 8 child slots:
+ *  kind[i*8+k]   : 0 empty, 1 interior, 2 leaf (own-box nodes: slots 0-1 are
+ *                  the two children (kind 1), or slot 0 is the node's own
+ *                  leaf range (kind 2));
+ *  a[i*8+k]      : child node index (interior) or first leaf entry (leaf);
+ *  c[i*8+k]      : leaf entry count (leaf) else 0;
+ *  boxes[(i*8+k)*6..]: decoded child box lo.xyz, hi.xyz (wide nodes);
+ *  own_boxes[i*6..]  : the node's own box (own-box nodes);
+ *  leaf_ids[j]   : triangle id of leaf entry j (n_leaf_entries values). */
+scion_status scion_debug_host_decode(scion_host_bvh hb, uint32_t *kind, uint32_t *a, uint32_t *c,
+                                     float *boxes, float *own_boxes, uint32_t *leaf_ids);
+
+void scion_debug_host_destroy(scion_host_bvh hb);
+
+/* Directed rounding of a float to IEEE binary16 (dir < 0: toward -inf,
+ * dir > 0: toward +inf), returned as the 16 bits; and the exact decode. */
+uint32_t scion_debug_f16_round(float x, int dir);
+float scion_debug_f16_decode(uint32_t h);
+
+/* Message of the last host-side error (static storage, not thread-safe). */
+const char *scion_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

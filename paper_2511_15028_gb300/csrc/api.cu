@@ -1,0 +1,402 @@
+// C ABI (include/scion.h, include/scion_debug.h): build, trace, status.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/scion.h"
+#include "../../include/scion_debug.h"
+#include "builder.h"
+#include "kernels.h"
+
+using namespace scion;
+
+struct scion_bvh_s {
+  scion_layout_desc desc;
+  bool own_box = false;
+  uint32_t n_tris = 0, n_verts = 0;
+  bool indexed = false;
+  uint32_t n_nodes = 0, node_stride = 0, n_leaf_entries = 0;
+  uint32_t root_ref = kEmptyRef, depth = 0, stack_need = 0;
+  uint64_t node_bytes = 0, node2_bytes = 0, prim_bytes = 0, idx_bytes = 0, vert_bytes = 0;
+  void *d_nodes = nullptr, *d_nodes2 = nullptr, *d_prims = nullptr, *d_prim_ids = nullptr;
+  void *d_verts = nullptr, *d_idx = nullptr;
+  uint32_t *d_scratch = nullptr;  // u64 work counter, u32 exit counter, u32 status
+  double build_ms = 0.0;
+  int device = 0;
+};
+
+namespace {
+
+std::string g_last_error;
+
+scion_status cuda_fail(cudaError_t e) {
+  g_last_error = cudaGetErrorString(e);
+  return SCION_ERR_CUDA;
+}
+
+#define SCION_CUDA(call)                                      \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) {                                  \
+      if (e_ == cudaErrorMemoryAllocation) {                  \
+        g_last_error = "out of device memory";                \
+        return SCION_ERR_OOM;                                 \
+      }                                                       \
+      return cuda_fail(e_);                                   \
+    }                                                         \
+  } while (0)
+
+void free_bvh(scion_bvh b) {
+  if (!b) return;
+  void *bufs[] = {b->d_nodes, b->d_nodes2, b->d_prims, b->d_prim_ids, b->d_verts, b->d_idx, b->d_scratch};
+  for (void *p : bufs)
+    if (p) cudaFree(p);
+  delete b;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+scion_status upload(void **dst, const std::vector<T> &src, cudaStream_t s, uint64_t *bytes) {
+  *bytes = src.size() * sizeof(T);
+  if (src.empty()) return SCION_OK;
+  SCION_CUDA(cudaMalloc(dst, *bytes));
+  SCION_CUDA(cudaMemcpyAsync(*dst, src.data(), *bytes, cudaMemcpyHostToDevice, s));
+  return SCION_OK;
+}
+
+TraceKernel pick_kernel(const scion_bvh b, int any) {
+  const scion_layout_desc &d = b->desc;
+  const int soa = (int)d.box_layout, cref = (int)d.child_ref;
+  if (b->own_box) return kernels_own(soa, cref, any);
+  switch (d.width * 10 + d.box_prec) {
+    case 20: return kernels_w2_p0(soa, cref, any);
+    case 21: return kernels_w2_p1(soa, cref, any);
+    case 22: return kernels_w2_p2(soa, cref, any);
+    case 40: return kernels_w4_p0(soa, cref, any);
+    case 41: return kernels_w4_p1(soa, cref, any);
+    case 42: return kernels_w4_p2(soa, cref, any);
+    case 80: return kernels_w8_p0(soa, cref, any);
+    case 81: return kernels_w8_p1(soa, cref, any);
+    case 82: return kernels_w8_p2(soa, cref, any);
+  }
+  return nullptr;
+}
+
+
+// Host half of scion_build: validate, build the logical BVH2, pack.
+scion_status build_host(const float *v, uint64_t n_verts, const uint32_t *ix, uint64_t n_tris,
+                        const scion_layout_desc *desc, HostBVH *hb) {
+  if (!desc || (n_tris > 0 && !v)) return SCION_ERR_INVALID_ARG;
+  if (n_tris >= kMaxPrims || n_verts >= (1ull << 32)) return SCION_ERR_INVALID_ARG;
+  if (!ix && n_verts != 3 * n_tris) return SCION_ERR_INVALID_ARG;
+  scion_layout_desc d;
+  bool own_box = false;
+  scion_status st = normalize_desc(*desc, &d, &own_box);
+  if (st != SCION_OK) return st;
+  if (ix)
+    for (uint64_t i = 0; i < 3 * n_tris; ++i)
+      if (ix[i] >= n_verts) return SCION_ERR_INVALID_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  BuildInput in{v, n_verts, ix, n_tris};
+  try {
+    LogicalBVH lb;
+    build_logical(in, d.sah_bins, d.leaf_max, &lb);
+    std::string err;
+    st = pack_bvh(in, lb, d, own_box, hb, &err);
+    if (st != SCION_OK) {
+      g_last_error = err;
+      return st;
+    }
+  } catch (const std::bad_alloc &) {
+    g_last_error = "out of host memory";
+    return SCION_ERR_OOM;
+  }
+  hb->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return SCION_OK;
+}
+
+uint64_t host_prim_bytes(const HostBVH &hb) {
+  return hb.prim_direct.size() * 4 + hb.prim_ids.size() * 4 +
+         (hb.desc.prim_ref == REF_INDIRECT ? hb.indices.size() * 4 : 0);
+}
+
+struct DevInfo {
+  int sms = 0;
+};
+std::mutex g_dev_mu;
+std::vector<DevInfo> g_dev;
+
+int device_sms(int dev) {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+  if (g_dev[dev].sms == 0) cudaDeviceGetAttribute(&g_dev[dev].sms, cudaDevAttrMultiProcessorCount, dev);
+  return g_dev[dev].sms;
+}
+
+scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *out,
+                          const scion_trace_params *params, cudaStream_t stream, int any) {
+  if (!b || (n > 0 && (!rays || !out))) return SCION_ERR_INVALID_ARG;
+  if (n == 0) return SCION_OK;
+  if ((reinterpret_cast<uintptr_t>(rays) & 15u) || (!any && (reinterpret_cast<uintptr_t>(out) & 15u)) ||
+      (any && (reinterpret_cast<uintptr_t>(out) & 3u)))
+    return SCION_ERR_INVALID_ARG;
+  scion_trace_params p{};
+  if (params) p = *params;
+  if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch != 0) return SCION_ERR_INVALID_ARG;
+  uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
+  if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
+  uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
+  if (smem_entries > 64) return SCION_ERR_INVALID_ARG;
+  if (p.ordered_children > 2) return SCION_ERR_INVALID_ARG;
+  const uint32_t ordered = p.ordered_children == 2 ? 0u : 1u;
+  TraceKernel k = pick_kernel(b, any);
+  if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  const size_t smem = (size_t)tpb * smem_entries * sizeof(uint2);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint32_t ctas = p.ctas_per_sm;
+  if (ctas == 0) {
+    int nb = 0;
+    SCION_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k, (int)tpb, smem));
+    ctas = (uint32_t)std::max(nb, 1);
+  }
+  if (smem > 48 * 1024)
+    SCION_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
+  TraceArgs a;
+  a.nodes = static_cast<const uint4 *>(b->d_nodes);
+  a.nodes2 = static_cast<const uint2 *>(b->d_nodes2);
+  a.prims = static_cast<const float4 *>(b->d_prims);
+  a.prim_ids = static_cast<const uint32_t *>(b->d_prim_ids);
+  a.verts = static_cast<const float4 *>(b->d_verts);
+  a.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+  a.rays = reinterpret_cast<const float4 *>(rays);
+  a.out = out;
+  a.n = n;
+  a.root_ref = b->root_ref;
+  a.n_nodes = b->n_nodes;
+  a.prim_indirect = b->desc.prim_ref;
+  a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
+  a.ordered = ordered;
+  a.smem_stack = smem_entries;
+  a.work = reinterpret_cast<unsigned long long *>(b->d_scratch);
+  a.exit_count = b->d_scratch + 2;
+  a.status = b->d_scratch + 3;
+  void *args[] = {&a};
+  SCION_CUDA(cudaLaunchKernel((const void *)k, dim3((unsigned)grid), dim3(tpb), args, smem, stream));
+  return SCION_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *scion_status_string(scion_status s) {
+  switch (s) {
+    case SCION_OK: return "ok";
+    case SCION_ERR_INVALID_ARG: return "invalid argument";
+    case SCION_ERR_UNSUPPORTED_LAYOUT: return "unsupported layout";
+    case SCION_ERR_OOM: return "out of memory";
+    case SCION_ERR_CUDA: return "CUDA error";
+    case SCION_ERR_STACK_OVERFLOW: return "traversal stack overflow";
+    case SCION_ERR_ITER_LIMIT: return "traversal step limit";
+    case SCION_ERR_BAD_INPUT: return "bad input";
+  }
+  return "unknown status";
+}
+
+const char *scion_last_error(void) { return g_last_error.c_str(); }
+
+scion_status scion_build(const float *verts, uint64_t n_verts, const uint32_t *indices,
+                         uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
+                         scion_bvh *out) {
+  if (!out) return SCION_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc || (n_tris > 0 && !verts)) return SCION_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // host copies of device-resident inputs (a device-to-host boundary)
+  std::vector<float> hv;
+  std::vector<uint32_t> hi;
+  const float *v = verts;
+  const uint32_t *ix = indices;
+  if (verts && is_device_ptr(verts)) {
+    hv.resize(3 * n_verts);
+    SCION_CUDA(cudaMemcpyAsync(hv.data(), verts, hv.size() * 4, cudaMemcpyDeviceToHost, s));
+    SCION_CUDA(cudaStreamSynchronize(s));
+    v = hv.data();
+  }
+  if (indices && is_device_ptr(indices)) {
+    hi.resize(3 * n_tris);
+    SCION_CUDA(cudaMemcpyAsync(hi.data(), indices, hi.size() * 4, cudaMemcpyDeviceToHost, s));
+    SCION_CUDA(cudaStreamSynchronize(s));
+    ix = hi.data();
+  }
+  HostBVH hb;
+  scion_status st = build_host(v, n_verts, ix, n_tris, desc, &hb);
+  if (st != SCION_OK) return st;
+  scion_bvh b = new (std::nothrow) scion_bvh_s();
+  if (!b) return SCION_ERR_OOM;
+  b->desc = hb.desc;
+  b->own_box = hb.own_box;
+  b->n_tris = (uint32_t)n_tris;
+  b->n_verts = (uint32_t)n_verts;
+  b->indexed = ix != nullptr;
+  b->n_nodes = hb.n_nodes;
+  b->node_stride = hb.node_stride;
+  b->n_leaf_entries = hb.n_leaf_entries;
+  b->root_ref = hb.root_ref;
+  b->depth = hb.depth;
+  b->stack_need = hb.stack_need;
+  b->build_ms = hb.build_ms;
+  cudaGetDevice(&b->device);
+  uint64_t pb = 0, pi = 0;
+  scion_status us = SCION_OK;
+  if (us == SCION_OK) us = upload(&b->d_nodes, hb.nodes, s, &b->node_bytes);
+  if (us == SCION_OK) us = upload(&b->d_nodes2, hb.nodes2, s, &b->node2_bytes);
+  if (us == SCION_OK) us = upload(&b->d_prims, hb.prim_direct, s, &pb);
+  if (us == SCION_OK) us = upload(&b->d_prim_ids, hb.prim_ids, s, &pi);
+  if (us == SCION_OK) us = upload(&b->d_verts, hb.verts4, s, &b->vert_bytes);
+  if (us == SCION_OK) us = upload(&b->d_idx, hb.indices, s, &b->idx_bytes);
+  if (us == SCION_OK) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_scratch), 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scratch, 0, 4 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) us = e == cudaErrorMemoryAllocation ? SCION_ERR_OOM : cuda_fail(e);
+  }
+  if (us != SCION_OK) {
+    free_bvh(b);
+    return us;
+  }
+  b->prim_bytes = host_prim_bytes(hb);
+  *out = b;
+  return SCION_OK;
+}
+
+scion_status scion_bvh_info(scion_bvh b, uint64_t *node_bytes, uint64_t *prim_bytes, uint32_t *depth,
+                            uint32_t *n_nodes) {
+  if (!b) return SCION_ERR_INVALID_ARG;
+  if (node_bytes) *node_bytes = b->node_bytes + b->node2_bytes;
+  if (prim_bytes) *prim_bytes = b->prim_bytes;
+  if (depth) *depth = b->depth;
+  if (n_nodes) *n_nodes = b->n_nodes;
+  return SCION_OK;
+}
+
+scion_status scion_trace_closest(scion_bvh b, const scion_ray *d_rays, uint64_t n, scion_hit *d_hits,
+                                 const scion_trace_params *params, scion_stream stream) {
+  return launch_trace(b, d_rays, n, d_hits, params, reinterpret_cast<cudaStream_t>(stream), 0);
+}
+
+scion_status scion_trace_any(scion_bvh b, const scion_ray *d_rays, uint64_t n, uint32_t *d_occluded,
+                             const scion_trace_params *params, scion_stream stream) {
+  return launch_trace(b, d_rays, n, d_occluded, params, reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+scion_status scion_get_status(scion_bvh b, scion_stream stream, scion_status *device_status) {
+  if (!b || !device_status) return SCION_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  SCION_CUDA(cudaMemcpyAsync(&v, b->d_scratch + 3, 4, cudaMemcpyDeviceToHost, s));
+  SCION_CUDA(cudaStreamSynchronize(s));
+  if (v) {
+    SCION_CUDA(cudaMemsetAsync(b->d_scratch + 3, 0, 4, s));
+    SCION_CUDA(cudaStreamSynchronize(s));
+  }
+  *device_status = (scion_status)v;
+  return SCION_OK;
+}
+
+void scion_destroy(scion_bvh b) { free_bvh(b); }
+
+// ---------------------------------------------------------------- debug ABI
+struct scion_host_bvh_s {
+  HostBVH hb;
+};
+
+scion_status scion_debug_build_host(const float *verts, uint64_t n_verts, const uint32_t *indices,
+                                    uint64_t n_tris, const scion_layout_desc *desc, scion_host_bvh *out) {
+  if (!out) return SCION_ERR_INVALID_ARG;
+  *out = nullptr;
+  scion_host_bvh h = new (std::nothrow) scion_host_bvh_s();
+  if (!h) return SCION_ERR_OOM;
+  scion_status st = build_host(verts, n_verts, indices, n_tris, desc, &h->hb);
+  if (st != SCION_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return SCION_OK;
+}
+
+scion_status scion_debug_host_stats(scion_host_bvh h, scion_debug_info *info) {
+  if (!h || !info) return SCION_ERR_INVALID_ARG;
+  const HostBVH &b = h->hb;
+  info->n_nodes = b.n_nodes;
+  info->node_stride = b.node_stride;
+  info->n_leaf_entries = b.n_leaf_entries;
+  info->root_ref = b.root_ref;
+  info->depth = b.depth;
+  info->stack_need = b.stack_need;
+  info->own_box = b.own_box ? 1u : 0u;
+  info->reserved = 0;
+  info->node_bytes = b.nodes.size() + b.nodes2.size();
+  info->prim_bytes = host_prim_bytes(b);
+  info->vert_bytes = b.verts4.size() * 4;
+  info->build_ms = b.build_ms;
+  return SCION_OK;
+}
+
+scion_status scion_debug_host_decode(scion_host_bvh h, uint32_t *kind, uint32_t *a, uint32_t *c,
+                                     float *boxes, float *own_boxes, uint32_t *leaf_ids) {
+  if (!h || !kind || !a || !c || !boxes || !own_boxes || !leaf_ids) return SCION_ERR_INVALID_ARG;
+  const HostBVH &hb = h->hb;
+  for (uint32_t i = 0; i < hb.n_nodes; ++i) {
+    DecodedChild ch[8];
+    Box3 own{};
+    std::memset(ch, 0, sizeof(ch));
+    const int nc = decode_node(hb, i, ch, &own);
+    for (int k = 0; k < 8; ++k) {
+      const size_t o = (size_t)i * 8 + k;
+      kind[o] = k < nc ? (uint32_t)ch[k].kind : 0u;
+      a[o] = ch[k].kind == 1 ? ch[k].node : ch[k].first;
+      c[o] = ch[k].kind == 2 ? ch[k].count : 0u;
+      for (int q = 0; q < 3; ++q) {
+        boxes[o * 6 + q] = ch[k].box.lo[q];
+        boxes[o * 6 + 3 + q] = ch[k].box.hi[q];
+      }
+    }
+    for (int q = 0; q < 3; ++q) {
+      own_boxes[(size_t)i * 6 + q] = own.lo[q];
+      own_boxes[(size_t)i * 6 + 3 + q] = own.hi[q];
+    }
+  }
+  for (uint32_t i = 0; i < hb.n_leaf_entries; ++i) {
+    if (hb.desc.prim_ref == REF_DIRECT) std::memcpy(&leaf_ids[i], &hb.prim_direct[(size_t)i * 12 + 3], 4);
+    else leaf_ids[i] = hb.prim_ids[i];
+  }
+  return SCION_OK;
+}
+
+void scion_debug_host_destroy(scion_host_bvh h) { delete h; }
+
+uint32_t scion_debug_f16_round(float x, int dir) {
+  return dir < 0 ? f32_to_f16_down(x) : f32_to_f16_up(x);
+}
+
+float scion_debug_f16_decode(uint32_t h) { return f16_to_f32((uint16_t)h); }
+
+}  // extern "C"

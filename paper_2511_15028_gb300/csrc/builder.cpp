@@ -1,0 +1,864 @@
+// Host-side BVH construction and packing. See builder.h.
+#include "builder.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <functional>
+#include <queue>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace scion {
+
+// ------------------------------------------------------------ rounding helpers
+float round_down_f32(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+float round_up_f32(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+float f16_to_f32(uint16_t h) {
+  uint32_t s = h >> 15, e = (h >> 10) & 31u, m = h & 1023u;
+  double v;
+  if (e == 0) v = std::ldexp((double)m, -24);
+  else if (e == 31) v = m ? NAN : INFINITY;
+  else v = std::ldexp((double)(1024u + m), (int)e - 25);
+  return (float)(s ? -v : v);
+}
+
+// IEEE binary16 with directed rounding: dir < 0 toward -inf, dir > 0 toward +inf.
+static uint16_t f16_directed(double x, int dir) {
+  if (std::isnan(x)) return 0x7E00;
+  if (x == 0.0) return std::signbit(x) ? 0x8000 : 0;
+  const bool neg = x < 0.0;
+  const double a = std::fabs(x);
+  uint16_t mag;  // largest finite f16 magnitude <= a
+  if (a >= 65504.0) {
+    mag = 0x7BFF;
+  } else {
+    int e;
+    std::frexp(a, &e);  // a = f * 2^e, f in [0.5, 1)
+    int E = e + 14;     // biased exponent of a normal f16 in [2^(E-15), 2^(E-14))
+    if (E >= 1) {
+      double f = std::floor((std::ldexp(a, 15 - E) - 1.0) * 1024.0);
+      mag = (uint16_t)((E << 10) | (int)f);
+    } else {
+      mag = (uint16_t)std::floor(std::ldexp(a, 24));
+    }
+  }
+  const bool exact = (double)f16_to_f32(mag) == a;
+  const bool away = (dir > 0 && !neg) || (dir < 0 && neg);
+  if (!exact && away) mag = (uint16_t)(mag + 1u);  // 0x7BFF + 1 = +inf pattern
+  return (uint16_t)((neg ? 0x8000u : 0u) | mag);
+}
+uint16_t f32_to_f16_down(float x) { return f16_directed(x, -1); }
+uint16_t f32_to_f16_up(float x) { return f16_directed(x, +1); }
+
+// ------------------------------------------------------------ descriptor
+scion_status normalize_desc(const scion_layout_desc &in, scion_layout_desc *out, bool *own_box) {
+  scion_layout_desc d = in;
+  if (d.reserved != 0) return SCION_ERR_INVALID_ARG;
+  if (d.width != 2 && d.width != 4 && d.width != 8) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  if (d.box_layout > 1 || d.box_prec > 2 || d.child_ref > 1 || d.prim_ref > 1 || d.order > 2)
+    return SCION_ERR_UNSUPPORTED_LAYOUT;
+  if (d.leaf_max == 0) d.leaf_max = 4;
+  if (d.leaf_max > kMaxLeaf) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  if (d.sah_bins == 0) d.sah_bins = 16;
+  if (d.sah_bins < 2 || d.sah_bins > 64) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  if (d.treelet_bytes == 0) d.treelet_bytes = 1024;
+  const bool ob = d.width == 2 && d.box_prec == PREC_F32;
+  if (ob && d.child_ref == REF_DIRECT && d.order != ORDER_DFS) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  *out = d;
+  *own_box = ob;
+  return SCION_OK;
+}
+
+// ------------------------------------------------------------ SAH BVH2
+namespace {
+
+struct PrimInfo {
+  float lo[3], hi[3], c[3];
+};
+
+inline void box_empty(Box3 &b) {
+  for (int a = 0; a < 3; ++a) { b.lo[a] = INFINITY; b.hi[a] = -INFINITY; }
+}
+inline void box_grow(Box3 &b, const float *lo, const float *hi) {
+  for (int a = 0; a < 3; ++a) {
+    b.lo[a] = std::min(b.lo[a], lo[a]);
+    b.hi[a] = std::max(b.hi[a], hi[a]);
+  }
+}
+inline void box_merge(Box3 &b, const Box3 &c) { box_grow(b, c.lo, c.hi); }
+// surface area in double: float products overflow for coordinates > ~1e19
+inline double box_area(const Box3 &b) {
+  double e0 = std::max(0.0, (double)b.hi[0] - (double)b.lo[0]);
+  double e1 = std::max(0.0, (double)b.hi[1] - (double)b.lo[1]);
+  double e2 = std::max(0.0, (double)b.hi[2] - (double)b.lo[2]);
+  return 2.0 * (e0 * e1 + e1 * e2 + e2 * e0);
+}
+
+constexpr int kMaxBins = 64;
+
+struct Bins {
+  uint32_t cnt[3][kMaxBins];
+  Box3 box[3][kMaxBins];
+  void clear(int nb) {
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < nb; ++k) { cnt[a][k] = 0; box_empty(box[a][k]); }
+  }
+};
+
+class SahBuilder {
+ public:
+  SahBuilder(const std::vector<PrimInfo> &info, uint32_t bins, uint32_t leaf_max, LogicalBVH *out)
+      : info_(info), bins_((int)bins), leaf_max_(leaf_max), out_(out) {}
+
+  void run() {
+    const uint32_t n = (uint32_t)out_->prims.size();
+    out_->nodes.assign(n ? 2 * (size_t)n - 1 : 0, LNode{});
+    next_ = 0;
+    if (n == 0) return;
+    struct Task { uint32_t id, first, count; };
+    std::vector<Task> big{{alloc(), 0, n}}, small;
+    const uint32_t kSerial = 1u << 16;
+    while (!big.empty()) {
+      Task t = big.back();
+      big.pop_back();
+      uint32_t l, r, mid;
+      if (!split_node(t.id, t.first, t.count, true, &l, &r, &mid)) continue;
+      Task lt{l, t.first, mid - t.first}, rt{r, mid, t.first + t.count - mid};
+      (lt.count > kSerial ? big : small).push_back(lt);
+      (rt.count > kSerial ? big : small).push_back(rt);
+    }
+    const long ns = (long)small.size();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long i = 0; i < ns; ++i) build_serial(small[i].id, small[i].first, small[i].count);
+    out_->nodes.resize(next_.load());
+  }
+
+ private:
+  uint32_t alloc() { return next_.fetch_add(1); }
+
+  void bounds(uint32_t first, uint32_t count, bool par, Box3 *nb, Box3 *cb) {
+    box_empty(*nb);
+    box_empty(*cb);
+    const uint32_t *p = out_->prims.data();
+    if (par && count > 4096) {
+#ifdef _OPENMP
+      const int nt = omp_get_max_threads();
+#else
+      const int nt = 1;
+#endif
+      std::vector<Box3> nbs(nt), cbs(nt);
+      for (int i = 0; i < nt; ++i) { box_empty(nbs[i]); box_empty(cbs[i]); }
+#pragma omp parallel for schedule(static)
+      for (long i = first; i < (long)(first + count); ++i) {
+#ifdef _OPENMP
+        const int tid = omp_get_thread_num();
+#else
+        const int tid = 0;
+#endif
+        const PrimInfo &q = info_[p[i]];
+        box_grow(nbs[tid], q.lo, q.hi);
+        box_grow(cbs[tid], q.c, q.c);
+      }
+      for (int i = 0; i < nt; ++i) { box_merge(*nb, nbs[i]); box_merge(*cb, cbs[i]); }
+      return;
+    }
+    for (uint32_t i = first; i < first + count; ++i) {
+      const PrimInfo &q = info_[p[i]];
+      box_grow(*nb, q.lo, q.hi);
+      box_grow(*cb, q.c, q.c);
+    }
+  }
+
+  inline int bin_of(const PrimInfo &q, int a, const Box3 &cb, float scale) const {
+    int k = (int)((q.c[a] - cb.lo[a]) * scale);
+    return std::min(std::max(k, 0), bins_ - 1);
+  }
+
+  void bin(uint32_t first, uint32_t count, const Box3 &cb, const float *scale, bool par, Bins *bn) {
+    bn->clear(bins_);
+    const uint32_t *p = out_->prims.data();
+    if (par && count > 4096) {
+#ifdef _OPENMP
+      const int nt = omp_get_max_threads();
+#else
+      const int nt = 1;
+#endif
+      std::vector<Bins> loc(nt);
+      for (auto &b : loc) b.clear(bins_);
+#pragma omp parallel for schedule(static)
+      for (long i = first; i < (long)(first + count); ++i) {
+#ifdef _OPENMP
+        Bins &b = loc[omp_get_thread_num()];
+#else
+        Bins &b = loc[0];
+#endif
+        const PrimInfo &q = info_[p[i]];
+        for (int a = 0; a < 3; ++a) {
+          if (!(scale[a] > 0.f)) continue;
+          int k = bin_of(q, a, cb, scale[a]);
+          b.cnt[a][k]++;
+          box_grow(b.box[a][k], q.lo, q.hi);
+        }
+      }
+      for (auto &b : loc)
+        for (int a = 0; a < 3; ++a)
+          for (int k = 0; k < bins_; ++k) {
+            bn->cnt[a][k] += b.cnt[a][k];
+            box_merge(bn->box[a][k], b.box[a][k]);
+          }
+      return;
+    }
+    for (uint32_t i = first; i < first + count; ++i) {
+      const PrimInfo &q = info_[p[i]];
+      for (int a = 0; a < 3; ++a) {
+        if (!(scale[a] > 0.f)) continue;
+        int k = bin_of(q, a, cb, scale[a]);
+        bn->cnt[a][k]++;
+        box_grow(bn->box[a][k], q.lo, q.hi);
+      }
+    }
+  }
+
+  // Decide leaf or split for node `id`; on a split allocate the children and
+  // partition the range. Returns false for a leaf.
+  bool split_node(uint32_t id, uint32_t first, uint32_t count, bool par, uint32_t *l,
+                  uint32_t *r, uint32_t *mid_out) {
+    LNode &nd = out_->nodes[id];
+    Box3 nb, cb;
+    bounds(first, count, par, &nb, &cb);
+    nd.box = nb;
+    float scale[3];
+    for (int a = 0; a < 3; ++a) {
+      float e = cb.hi[a] - cb.lo[a];
+      scale[a] = e > 0.f ? (float)bins_ / e : 0.f;
+    }
+    int best_axis = -1, best_bin = -1;
+    double best_cost = INFINITY;
+    if (count > 1) {
+      Bins bn;
+      bin(first, count, cb, scale, par, &bn);
+      for (int a = 0; a < 3; ++a) {
+        if (!(scale[a] > 0.f)) continue;
+        double rarea[kMaxBins];
+        uint32_t rcnt[kMaxBins];
+        Box3 acc;
+        box_empty(acc);
+        uint32_t n = 0;
+        for (int k = bins_ - 1; k > 0; --k) {
+          box_merge(acc, bn.box[a][k]);
+          n += bn.cnt[a][k];
+          rarea[k] = box_area(acc);
+          rcnt[k] = n;
+        }
+        box_empty(acc);
+        n = 0;
+        for (int k = 0; k < bins_ - 1; ++k) {
+          box_merge(acc, bn.box[a][k]);
+          n += bn.cnt[a][k];
+          if (n == 0 || rcnt[k + 1] == 0) continue;
+          double c = box_area(acc) * (double)n + rarea[k + 1] * (double)rcnt[k + 1];
+          if (c < best_cost) { best_cost = c; best_axis = a; best_bin = k; }
+        }
+      }
+    }
+    const double area = box_area(nb);
+    const double leaf_cost = area * (double)count;
+    const double split_cost = area + best_cost;
+    if (count == 1 || (count <= leaf_max_ && (best_axis < 0 || leaf_cost <= split_cost))) {
+      nd.first = first;
+      nd.count = count;
+      nd.left = nd.right = 0;
+      nd.axis = 0;
+      return false;
+    }
+    uint32_t *p = out_->prims.data();
+    uint32_t mid;
+    int axis = best_axis;
+    if (best_axis < 0) {
+      mid = first + count / 2;
+      float ext = -1.f;
+      for (int a = 0; a < 3; ++a)
+        if (nb.hi[a] - nb.lo[a] > ext) { ext = nb.hi[a] - nb.lo[a]; axis = a; }
+    } else {
+      uint32_t *m = std::partition(p + first, p + first + count, [&](uint32_t q) {
+        return bin_of(info_[q], best_axis, cb, scale[best_axis]) <= best_bin;
+      });
+      mid = (uint32_t)(m - p);
+      if (mid == first || mid == first + count) mid = first + count / 2;
+    }
+    nd.count = 0;
+    nd.first = 0;
+    nd.axis = (uint32_t)std::max(axis, 0);
+    nd.left = alloc();
+    nd.right = alloc();
+    *l = nd.left;
+    *r = nd.right;
+    *mid_out = mid;
+    return true;
+  }
+
+  void build_serial(uint32_t id, uint32_t first, uint32_t count) {
+    uint32_t l, r, mid;
+    if (!split_node(id, first, count, false, &l, &r, &mid)) return;
+    build_serial(l, first, mid - first);
+    build_serial(r, mid, first + count - mid);
+  }
+
+  const std::vector<PrimInfo> &info_;
+  int bins_;
+  uint32_t leaf_max_;
+  LogicalBVH *out_;
+  std::atomic<uint32_t> next_{0};
+};
+
+inline bool finite_tri(const float *v0, const float *v1, const float *v2) {
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(v0[k]) || !std::isfinite(v1[k]) || !std::isfinite(v2[k])) return false;
+  return true;
+}
+
+inline void tri_verts(const BuildInput &in, uint64_t t, const float **v0, const float **v1,
+                      const float **v2) {
+  if (in.indices) {
+    *v0 = in.verts + 3 * (uint64_t)in.indices[3 * t];
+    *v1 = in.verts + 3 * (uint64_t)in.indices[3 * t + 1];
+    *v2 = in.verts + 3 * (uint64_t)in.indices[3 * t + 2];
+  } else {
+    *v0 = in.verts + 9 * t;
+    *v1 = in.verts + 9 * t + 3;
+    *v2 = in.verts + 9 * t + 6;
+  }
+}
+
+}  // namespace
+
+void build_logical(const BuildInput &in, uint32_t bins, uint32_t leaf_max, LogicalBVH *out) {
+  const uint64_t n = in.n_tris;
+  std::vector<PrimInfo> info(n);
+  std::vector<uint8_t> ok(n);
+#pragma omp parallel for schedule(static)
+  for (long long t = 0; t < (long long)n; ++t) {
+    const float *v0, *v1, *v2;
+    tri_verts(in, (uint64_t)t, &v0, &v1, &v2);
+    ok[t] = finite_tri(v0, v1, v2);
+    PrimInfo &q = info[t];
+    for (int a = 0; a < 3; ++a) {
+      q.lo[a] = std::min(v0[a], std::min(v1[a], v2[a]));
+      q.hi[a] = std::max(v0[a], std::max(v1[a], v2[a]));
+      q.c[a] = (v0[a] + v1[a] + v2[a]) * (1.0f / 3.0f);
+    }
+  }
+  out->prims.clear();
+  out->prims.reserve(n);
+  for (uint64_t t = 0; t < n; ++t)
+    if (ok[t]) out->prims.push_back((uint32_t)t);
+  SahBuilder b(info, bins, leaf_max, out);
+  b.run();
+}
+
+// ------------------------------------------------------------ node orders
+namespace {
+
+// Abstract tree of physical nodes: kids[i] lists the physical-node children
+// of node i (in slot order); area[i] its surface area. Node 0 is the root.
+struct OrderTree {
+  std::vector<std::vector<uint32_t>> kids;
+  std::vector<float> area;
+};
+
+std::vector<uint32_t> order_nodes(const OrderTree &t, uint32_t order, bool group_siblings,
+                                  uint32_t stride, uint32_t treelet_bytes) {
+  const size_t n = t.kids.size();
+  std::vector<uint32_t> out;
+  out.reserve(n);
+  if (n == 0) return out;
+  if (order == ORDER_BFS) {
+    std::deque<uint32_t> q{0};
+    while (!q.empty()) {
+      uint32_t x = q.front();
+      q.pop_front();
+      out.push_back(x);
+      for (uint32_t c : t.kids[x]) q.push_back(c);
+    }
+    return out;
+  }
+  if (order == ORDER_DFS) {
+    std::vector<uint32_t> st{0};
+    if (!group_siblings) {
+      while (!st.empty()) {
+        uint32_t x = st.back();
+        st.pop_back();
+        out.push_back(x);
+        for (size_t k = t.kids[x].size(); k-- > 0;) st.push_back(t.kids[x][k]);
+      }
+    } else {
+      out.push_back(0);
+      while (!st.empty()) {
+        uint32_t x = st.back();
+        st.pop_back();
+        for (uint32_t c : t.kids[x]) out.push_back(c);
+        for (size_t k = t.kids[x].size(); k-- > 0;) st.push_back(t.kids[x][k]);
+      }
+    }
+    return out;
+  }
+  // Treelets: grow a cluster from a root by repeatedly adding the frontier
+  // node (or sibling group) of largest surface area while the cluster fits the
+  // byte budget; what is left on the frontier seeds later clusters.
+  using Item = std::pair<float, uint32_t>;
+  if (!group_siblings) {
+    std::deque<uint32_t> roots{0};
+    while (!roots.empty()) {
+      uint32_t r = roots.front();
+      roots.pop_front();
+      std::priority_queue<Item> fr;
+      out.push_back(r);
+      uint32_t bytes = stride;
+      for (uint32_t c : t.kids[r]) fr.push({t.area[c], c});
+      while (!fr.empty() && bytes + stride <= treelet_bytes) {
+        uint32_t c = fr.top().second;
+        fr.pop();
+        out.push_back(c);
+        bytes += stride;
+        for (uint32_t g : t.kids[c]) fr.push({t.area[g], g});
+      }
+      std::vector<Item> rest;
+      while (!fr.empty()) { rest.push_back(fr.top()); fr.pop(); }
+      for (auto &it : rest) roots.push_back(it.second);
+    }
+    return out;
+  }
+  // groups are identified by their parent node
+  out.push_back(0);
+  std::deque<uint32_t> roots;
+  if (!t.kids[0].empty()) roots.push_back(0);
+  while (!roots.empty()) {
+    uint32_t gp = roots.front();
+    roots.pop_front();
+    std::priority_queue<Item> fr;
+    uint32_t bytes = 0;
+    auto emit = [&](uint32_t parent) {
+      for (uint32_t c : t.kids[parent]) out.push_back(c);
+      bytes += stride * (uint32_t)t.kids[parent].size();
+      for (uint32_t c : t.kids[parent])
+        if (!t.kids[c].empty()) fr.push({t.area[c], c});
+    };
+    emit(gp);
+    while (!fr.empty()) {
+      uint32_t c = fr.top().second;
+      if (bytes + stride * (uint32_t)t.kids[c].size() > treelet_bytes) break;
+      fr.pop();
+      emit(c);
+    }
+    std::vector<Item> rest;
+    while (!fr.empty()) { rest.push_back(fr.top()); fr.pop(); }
+    for (auto &it : rest) roots.push_back(it.second);
+  }
+  return out;
+}
+
+float area_of(const Box3 &b) { return (float)box_area(b); }
+
+// World-space pad: 2^-20 * (largest extent + largest |coordinate|), applied
+// outward before any encoding so that the traversal's float slab test (with
+// its relative margin) never culls a box whose triangle the intersector hits.
+Box3 padded(const Box3 &b) {
+  double ext = 0.0, mag = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    ext = std::max(ext, (double)b.hi[a] - (double)b.lo[a]);
+    mag = std::max(mag, std::max(std::fabs((double)b.lo[a]), std::fabs((double)b.hi[a])));
+  }
+  const double pad = std::ldexp(ext + mag, -20);
+  Box3 o;
+  for (int a = 0; a < 3; ++a) {
+    o.lo[a] = round_down_f32((double)b.lo[a] - pad);
+    o.hi[a] = round_up_f32((double)b.hi[a] + pad);
+  }
+  return o;
+}
+
+inline void put_u32(uint8_t *p, uint32_t v) { std::memcpy(p, &v, 4); }
+inline void put_f32(uint8_t *p, float v) { std::memcpy(p, &v, 4); }
+inline void put_u16(uint8_t *p, uint16_t v) { std::memcpy(p, &v, 2); }
+inline uint32_t get_u32(const uint8_t *p) { uint32_t v; std::memcpy(&v, p, 4); return v; }
+inline float get_f32(const uint8_t *p) { float v; std::memcpy(&v, p, 4); return v; }
+inline uint16_t get_u16(const uint8_t *p) { uint16_t v; std::memcpy(&v, p, 2); return v; }
+
+// u8 frame decode: coordinate = fma(q, 2^e, origin), the device arithmetic.
+inline float u8_decode(uint32_t q, float scale, float origin) {
+  return std::fma((float)q, scale, origin);
+}
+
+void emit_prims(const BuildInput &in, const LogicalBVH &lb, const LNode &leaf, HostBVH *out) {
+  for (uint32_t i = leaf.first; i < leaf.first + leaf.count; ++i) {
+    const uint32_t id = lb.prims[i];
+    if (out->desc.prim_ref == REF_DIRECT) {
+      const float *v0, *v1, *v2;
+      tri_verts(in, id, &v0, &v1, &v2);
+      float rec[12] = {v0[0], v0[1], v0[2], 0.f, v1[0], v1[1], v1[2], 0.f, v2[0], v2[1], v2[2], 0.f};
+      std::memcpy(&rec[3], &id, 4);
+      out->prim_direct.insert(out->prim_direct.end(), rec, rec + 12);
+    } else {
+      out->prim_ids.push_back(id);
+    }
+    out->n_leaf_entries++;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ packing
+scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_layout_desc &desc,
+                      bool own_box, HostBVH *out, std::string *err) {
+  out->desc = desc;
+  out->own_box = own_box;
+  out->n_tris = (uint32_t)in.n_tris;
+  out->n_verts = (uint32_t)in.n_verts;
+  out->indexed = in.indices != nullptr;
+  out->n_leaf_entries = 0;
+  // vertex / index tables (used by indirect prims and by the backward pass)
+  out->verts4.assign(4 * (size_t)in.n_verts, 0.f);
+  for (uint64_t v = 0; v < in.n_verts; ++v)
+    for (int k = 0; k < 3; ++k) out->verts4[4 * v + k] = in.verts[3 * v + k];
+  if (in.indices) out->indices.assign(in.indices, in.indices + 3 * in.n_tris);
+  const uint32_t W = desc.width;
+  const size_t nl = lb.nodes.size();
+  if (nl == 0) {  // no hittable triangle
+    out->n_nodes = 0;
+    out->root_ref = kEmptyRef;
+    out->depth = 0;
+    out->stack_need = 0;
+    return SCION_OK;
+  }
+
+  if (own_box) {
+    // ---- own-box binary nodes: every logical node is a physical node
+    OrderTree t;
+    t.kids.resize(nl);
+    t.area.resize(nl);
+    for (size_t i = 0; i < nl; ++i) {
+      t.area[i] = area_of(lb.nodes[i].box);
+      if (lb.nodes[i].count == 0) t.kids[i] = {lb.nodes[i].left, lb.nodes[i].right};
+    }
+    const bool group = desc.child_ref == REF_INDIRECT;
+    std::vector<uint32_t> ord = order_nodes(t, desc.order, group, kBinNodeBytes, desc.treelet_bytes);
+    std::vector<uint32_t> phys(nl);
+    for (size_t i = 0; i < ord.size(); ++i) phys[ord[i]] = (uint32_t)i;
+    // count pass: nodes = nl, prims = leaf entries; one allocation per buffer
+    out->n_nodes = (uint32_t)nl;
+    const bool soa = desc.box_layout == LAYOUT_SOA;
+    out->node_stride = soa ? kBinBoxBytes : kBinNodeBytes;
+    out->nodes.assign((size_t)nl * out->node_stride, 0);
+    if (soa) out->nodes2.assign((size_t)nl * kBinRefBytes, 0);
+    // fill pass in physical order
+    std::vector<uint32_t> depth(nl, 1);
+    uint32_t maxd = 1;
+    for (size_t pi = 0; pi < nl; ++pi) {
+      const uint32_t li = ord[pi];
+      const LNode &nd = lb.nodes[li];
+      const Box3 b = padded(nd.box);
+      uint32_t ref, meta;
+      if (nd.count > 0) {
+        ref = out->n_leaf_entries;
+        meta = bin_pack_meta(nd.count, 0);
+        emit_prims(in, lb, nd, out);
+      } else {
+        const uint32_t l = phys[nd.left], r = phys[nd.right];
+        if (desc.child_ref == REF_DIRECT) {
+          if (l != pi + 1) { *err = "DFS order violated"; return SCION_ERR_UNSUPPORTED_LAYOUT; }
+          ref = r - (uint32_t)pi;
+        } else {
+          if (r != l + 1) { *err = "siblings not contiguous"; return SCION_ERR_UNSUPPORTED_LAYOUT; }
+          ref = l;
+        }
+        meta = bin_pack_meta(0, nd.axis);
+        depth[nd.left] = depth[nd.right] = depth[li] + 1;
+        maxd = std::max(maxd, depth[li] + 1);
+      }
+      uint8_t *p = out->nodes.data() + pi * out->node_stride;
+      for (int a = 0; a < 3; ++a) {
+        put_f32(p + 4 * a, b.lo[a]);
+        put_f32(p + 12 + 4 * a, b.hi[a]);
+      }
+      uint8_t *q = soa ? out->nodes2.data() + pi * kBinRefBytes : p + 24;
+      put_u32(q, ref);
+      put_u32(q + 4, meta);
+    }
+    out->root_ref = 0;
+    out->depth = maxd;
+    out->stack_need = maxd;
+    return SCION_OK;
+  }
+
+  // ---- children-in-parent wide nodes: collapse the BVH2 to width W
+  std::vector<WNode> wn;
+  std::vector<uint32_t> wide_of(nl, kEmptyRef);
+  {
+    std::vector<uint32_t> todo{0};
+    wide_of[0] = 0;
+    wn.push_back(WNode{});
+    while (!todo.empty()) {
+      const uint32_t li = todo.back();
+      todo.pop_back();
+      const uint32_t wi = wide_of[li];
+      std::vector<uint32_t> ch;
+      if (lb.nodes[li].count > 0) {
+        ch.push_back(li);  // a leaf root: one-child wide root
+      } else {
+        ch = {lb.nodes[li].left, lb.nodes[li].right};
+        while (ch.size() < W) {
+          int best = -1;
+          float ba = -1.f;
+          for (size_t k = 0; k < ch.size(); ++k) {
+            const LNode &c = lb.nodes[ch[k]];
+            if (c.count == 0 && area_of(c.box) > ba) { ba = area_of(c.box); best = (int)k; }
+          }
+          if (best < 0) break;
+          const LNode &c = lb.nodes[ch[best]];
+          ch[best] = c.left;
+          ch.insert(ch.begin() + best + 1, c.right);
+        }
+      }
+      WNode w{};
+      w.lnode = li;
+      w.n = (uint32_t)ch.size();
+      for (size_t k = 0; k < ch.size(); ++k) {
+        w.child[k] = ch[k];
+        if (lb.nodes[ch[k]].count == 0 && ch[k] != li) {
+          wide_of[ch[k]] = (uint32_t)wn.size();
+          wn.push_back(WNode{});
+          todo.push_back(ch[k]);
+        }
+      }
+      wn[wi] = w;
+    }
+  }
+  const size_t nw = wn.size();
+  OrderTree t;
+  t.kids.resize(nw);
+  t.area.resize(nw);
+  for (size_t i = 0; i < nw; ++i) {
+    t.area[i] = area_of(lb.nodes[wn[i].lnode].box);
+    for (uint32_t k = 0; k < wn[i].n; ++k) {
+      const uint32_t c = wn[i].child[k];
+      if (lb.nodes[c].count == 0) t.kids[i].push_back(wide_of[c]);
+    }
+  }
+  const uint32_t prec = desc.box_prec, soa = desc.box_layout, cref = desc.child_ref;
+  const uint32_t stride = wide_node_stride(W, prec, cref);
+  std::vector<uint32_t> ord = order_nodes(t, desc.order, cref == REF_INDIRECT, stride, desc.treelet_bytes);
+  std::vector<uint32_t> phys(nw);
+  for (size_t i = 0; i < ord.size(); ++i) phys[ord[i]] = (uint32_t)i;
+  if (nw >= kMaxNodes) { *err = "too many nodes"; return SCION_ERR_INVALID_ARG; }
+  out->n_nodes = (uint32_t)nw;
+  out->node_stride = stride;
+  out->nodes.assign((size_t)nw * stride, 0);
+  std::vector<uint32_t> depth(nw, 1);
+  uint32_t maxd = 1;
+  const uint32_t ref_off = wide_ref_offset(W, prec);
+  for (size_t pi = 0; pi < nw; ++pi) {
+    const uint32_t wi = ord[pi];
+    const WNode &w = wn[wi];
+    uint8_t *p = out->nodes.data() + pi * stride;
+    Box3 cb[8];
+    for (uint32_t k = 0; k < w.n; ++k) cb[k] = padded(lb.nodes[w.child[k]].box);
+    // references and leaf primitives (slot order)
+    uint32_t first_interior = kEmptyRef, first_prim = kEmptyRef, rank = 0;
+    for (uint32_t k = 0; k < W; ++k) {
+      uint32_t refv = kEmptyRef, meta = 0;
+      if (k < w.n) {
+        const LNode &c = lb.nodes[w.child[k]];
+        if (c.count == 0) {
+          const uint32_t cp = phys[wide_of[w.child[k]]];
+          if (first_interior == kEmptyRef) first_interior = cp;
+          if (cref == REF_INDIRECT && cp != first_interior + rank) {
+            *err = "siblings not contiguous";
+            return SCION_ERR_UNSUPPORTED_LAYOUT;
+          }
+          refv = ref_interior(cp);
+          meta = kMetaInterior | rank;
+          ++rank;
+          depth[wide_of[w.child[k]]] = depth[wi] + 1;
+          maxd = std::max(maxd, depth[wi] + 1);
+        } else {
+          const uint32_t fp = out->n_leaf_entries;
+          if (first_prim == kEmptyRef) first_prim = fp;
+          refv = ref_leaf(fp, c.count);
+          meta = c.count;
+          emit_prims(in, lb, c, out);
+        }
+      }
+      if (cref == REF_DIRECT) put_u32(p + ref_off + 4 * k, refv);
+      else p[ref_off + 8 + k] = (uint8_t)meta;
+    }
+    if (cref == REF_INDIRECT) {
+      put_u32(p + ref_off, first_interior == kEmptyRef ? 0u : first_interior);
+      put_u32(p + ref_off + 4, first_prim == kEmptyRef ? 0u : first_prim);
+    }
+    // boxes
+    if (prec == PREC_F32) {
+      for (uint32_t k = 0; k < W; ++k)
+        for (uint32_t c = 0; c < 6; ++c) {
+          float v = k < w.n ? (c < 3 ? cb[k].lo[c] : cb[k].hi[c - 3]) : (c < 3 ? INFINITY : -INFINITY);
+          put_f32(p + wide_box_offset(W, prec, soa, k, c), v);
+        }
+    } else if (prec == PREC_F16) {
+      for (uint32_t k = 0; k < W; ++k)
+        for (uint32_t c = 0; c < 6; ++c) {
+          uint16_t h;
+          if (k < w.n) {
+            h = c < 3 ? f32_to_f16_down(cb[k].lo[c]) : f32_to_f16_up(cb[k].hi[c - 3]);
+            const float dec = f16_to_f32(h);
+            const bool ok = c < 3 ? dec <= cb[k].lo[c] : dec >= cb[k].hi[c - 3];
+            if (!ok) { *err = "f16 enclosure"; return SCION_ERR_BAD_INPUT; }
+          } else {
+            h = c < 3 ? 0x7C00 : 0xFC00;  // +inf / -inf: empty
+          }
+          put_u16(p + wide_box_offset(W, prec, soa, k, c), h);
+        }
+    } else {
+      // u8 relative to the merged child box (App. D.2), with a guard band of
+      // 2^-20 (|coordinate| + extent) beyond the padded boxes, power-of-two
+      // scale per axis, and verify-and-bump against the device decode.
+      double mlo[3], mhi[3];
+      for (int a = 0; a < 3; ++a) {
+        mlo[a] = INFINITY;
+        mhi[a] = -INFINITY;
+        for (uint32_t k = 0; k < w.n; ++k) {
+          mlo[a] = std::min(mlo[a], (double)cb[k].lo[a]);
+          mhi[a] = std::max(mhi[a], (double)cb[k].hi[a]);
+        }
+      }
+      double g = 0.0, mag = 0.0, ext = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        mag = std::max(mag, std::max(std::fabs(mlo[a]), std::fabs(mhi[a])));
+        ext = std::max(ext, mhi[a] - mlo[a]);
+      }
+      g = std::ldexp(mag + ext, -20);
+      float origin[3], scale[3];
+      uint8_t ebyte[3];
+      for (int a = 0; a < 3; ++a) {
+        origin[a] = round_down_f32(mlo[a] - g);
+        const double fhi = (double)round_up_f32(mhi[a] + g);
+        const double span = fhi - (double)origin[a];
+        int e = -126;
+        if (span > 0.0) {
+          int ex;
+          std::frexp(span / 255.0, &ex);  // span/255 < 2^ex
+          e = std::max(-126, ex - 2);
+        }
+        while (e < 127 && std::ldexp(255.0, e) < span) ++e;
+        ebyte[a] = (uint8_t)(e + 127);
+        scale[a] = (float)std::ldexp(1.0, e);
+        put_f32(p + 4 * a, origin[a]);
+        p[12 + a] = ebyte[a];
+      }
+      for (uint32_t k = 0; k < W; ++k)
+        for (int a = 0; a < 3; ++a) {
+          uint32_t qlo = 255, qhi = 0;
+          if (k < w.n) {
+            const double tlo = (double)cb[k].lo[a] - g, thi = (double)cb[k].hi[a] + g;
+            double fl = std::floor((tlo - origin[a]) / scale[a]);
+            double fh = std::ceil((thi - origin[a]) / scale[a]);
+            qlo = (uint32_t)std::min(255.0, std::max(0.0, fl));
+            qhi = (uint32_t)std::min(255.0, std::max(0.0, fh));
+            while (qlo > 0 && (double)u8_decode(qlo, scale[a], origin[a]) > tlo) --qlo;
+            while (qhi < 255 && (double)u8_decode(qhi, scale[a], origin[a]) < thi) ++qhi;
+            if ((double)u8_decode(qlo, scale[a], origin[a]) > tlo ||
+                (double)u8_decode(qhi, scale[a], origin[a]) < thi) {
+              *err = "u8 enclosure";
+              return SCION_ERR_BAD_INPUT;
+            }
+          }
+          p[wide_box_offset(W, prec, soa, k, a)] = (uint8_t)qlo;
+          p[wide_box_offset(W, prec, soa, k, 3 + a)] = (uint8_t)qhi;
+        }
+    }
+  }
+  out->root_ref = ref_interior(0);
+  out->depth = maxd;
+  out->stack_need = (W - 1) * maxd + 1;
+  return SCION_OK;
+}
+
+// ------------------------------------------------------------ decode (round trip)
+int decode_node(const HostBVH &b, uint32_t node, DecodedChild *ch, Box3 *own) {
+  const scion_layout_desc &d = b.desc;
+  if (node >= b.n_nodes) return -1;
+  if (b.own_box) {
+    const bool soa = d.box_layout == LAYOUT_SOA;
+    const uint8_t *p = b.nodes.data() + (size_t)node * b.node_stride;
+    const uint8_t *q = soa ? b.nodes2.data() + (size_t)node * kBinRefBytes : p + 24;
+    for (int a = 0; a < 3; ++a) {
+      own->lo[a] = get_f32(p + 4 * a);
+      own->hi[a] = get_f32(p + 12 + 4 * a);
+    }
+    const uint32_t ref = get_u32(q), meta = get_u32(q + 4);
+    const uint32_t cnt = bin_meta_count(meta);
+    if (cnt > 0) {
+      ch[0].kind = 2;
+      ch[0].first = ref;
+      ch[0].count = cnt;
+      return 1;
+    }
+    const uint32_t l = d.child_ref == REF_DIRECT ? node + 1 : ref;
+    const uint32_t r = d.child_ref == REF_DIRECT ? node + ref : ref + 1;
+    ch[0].kind = 1; ch[0].node = l;
+    ch[1].kind = 1; ch[1].node = r;
+    return 2;
+  }
+  const uint32_t W = d.width, prec = d.box_prec, soa = d.box_layout, cref = d.child_ref;
+  const uint8_t *p = b.nodes.data() + (size_t)node * b.node_stride;
+  const uint32_t ref_off = wide_ref_offset(W, prec);
+  uint32_t leaf_acc = 0;
+  for (uint32_t k = 0; k < W; ++k) {
+    DecodedChild &c = ch[k];
+    c.kind = 0;
+    if (cref == REF_DIRECT) {
+      const uint32_t r = get_u32(p + ref_off + 4 * k);
+      if (r == kEmptyRef) continue;
+      if (ref_is_interior(r)) { c.kind = 1; c.node = ref_node(r); }
+      else { c.kind = 2; c.first = ref_leaf_first(r); c.count = ref_leaf_count(r); }
+    } else {
+      const uint32_t bn = get_u32(p + ref_off), bp = get_u32(p + ref_off + 4);
+      const uint32_t m = p[ref_off + 8 + k];
+      if (m == 0) continue;
+      if (m & kMetaInterior) { c.kind = 1; c.node = bn + (m & 0x7Fu); }
+      else { c.kind = 2; c.first = bp + leaf_acc; c.count = m; leaf_acc += m; }
+    }
+    for (uint32_t a = 0; a < 3; ++a) {
+      const uint32_t olo = wide_box_offset(W, prec, soa, k, a), ohi = wide_box_offset(W, prec, soa, k, 3 + a);
+      if (prec == PREC_F32) {
+        c.box.lo[a] = get_f32(p + olo);
+        c.box.hi[a] = get_f32(p + ohi);
+      } else if (prec == PREC_F16) {
+        c.box.lo[a] = f16_to_f32(get_u16(p + olo));
+        c.box.hi[a] = f16_to_f32(get_u16(p + ohi));
+      } else {
+        const float origin = get_f32(p + 4 * a);
+        uint32_t bits = (uint32_t)p[12 + a] << 23;
+        float scale;
+        std::memcpy(&scale, &bits, 4);
+        c.box.lo[a] = u8_decode(p[olo], scale, origin);
+        c.box.hi[a] = u8_decode(p[ohi], scale, origin);
+      }
+    }
+  }
+  return (int)W;
+}
+
+}  // namespace scion

@@ -1,0 +1,471 @@
+// Layout-polymorphic closest-hit / any-hit traversal for sm_103a.
+//
+// One traversal loop (the closest_hit of Fig. 4 / App. G: test bounds, cull on
+// distmin against the best hit, descend, loop the leaf's triangles) is
+// instantiated per physical layout: the node codec (own-box binary node or
+// children-in-parent wide node of width W with f32/f16/u8 boxes, AoS or SoA,
+// direct or indirect child references) is a set of template parameters, so
+// every field access compiles to fixed offsets into registers loaded with
+// 128-bit non-coherent loads.
+//
+// Execution model: a persistent grid (a few CTAs per SM); each warp takes 32
+// rays at a time from a global counter with one atomicAdd; each lane traces
+// one ray with a per-thread stack whose first entries live in shared memory
+// (strided by blockDim, conflict-free) and whose tail spills to local memory.
+// The current entry is always in registers.
+//
+// Arithmetic: the box test only has to be conservative; the triangle test is
+// pinned bit for bit (see tri_test). Translation units are compiled with
+// --fmad=false so that only the explicit fmaf calls fuse.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/scion.h"
+#include "layout.h"
+
+namespace scion {
+
+struct TraceArgs {
+  const uint4 *nodes;       // node buffer (AoS nodes, or own-box SoA boxes)
+  const uint2 *nodes2;      // own-box SoA reference array
+  const float4 *prims;      // direct primitives, 3 float4 per entry
+  const uint32_t *prim_ids; // indirect primitives
+  const float4 *verts;      // float4 vertex table
+  const uint32_t *tri_idx;  // u32[3] per triangle, or null for a soup
+  const float4 *rays;       // 2 float4 per ray
+  void *out;                // scion_hit[n] (uint4) or uint32[n]
+  unsigned long long n;
+  uint32_t root_ref;
+  uint32_t n_nodes;
+  uint32_t prim_indirect;
+  uint32_t max_steps;
+  uint32_t ordered;
+  uint32_t smem_stack;      // shared-memory stack entries per thread
+  unsigned long long *work; // persistent work counter (self-resetting)
+  uint32_t *exit_count;     // CTAs finished (self-resetting)
+  uint32_t *status;         // first device error code
+};
+
+constexpr int kLocalStack = 48;           // local-memory tail of the stack
+constexpr float kTMargin = 9.5367431640625e-07f;  // 2^-20, relative slab widening
+constexpr uint32_t kErrStack = 5, kErrIter = 6;   // scion_status codes
+
+// ------------------------------------------------------------------ ray state
+struct Ray {
+  float ox, oy, oz, tmin, dx, dy, dz, tmax;
+  // box test: reciprocal direction (zero components replaced by a tiny
+  // signed value), o * rdir, and which plane is near per axis
+  float rx, ry, rz, orx, ory, orz;
+  bool nx, ny, nz;
+  // watertight test: permuted axes and shear constants
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float sel3(float x, float y, float z, int k) {
+  return k == 0 ? x : (k == 1 ? y : z);
+}
+
+__device__ __forceinline__ float safe_rcp(float d) {
+  const float dd = d == 0.0f ? copysignf(1e-30f, d) : d;
+  return __fdiv_rn(1.0f, dd);
+}
+
+__device__ __forceinline__ void setup_ray(const float4 a, const float4 b, Ray &r) {
+  r.ox = a.x; r.oy = a.y; r.oz = a.z; r.tmin = a.w;
+  r.dx = b.x; r.dy = b.y; r.dz = b.z; r.tmax = b.w;
+  r.rx = safe_rcp(r.dx); r.ry = safe_rcp(r.dy); r.rz = safe_rcp(r.dz);
+  r.orx = __fmul_rn(r.ox, r.rx); r.ory = __fmul_rn(r.oy, r.ry); r.orz = __fmul_rn(r.oz, r.rz);
+  r.nx = r.rx < 0.0f; r.ny = r.ry < 0.0f; r.nz = r.rz < 0.0f;
+  // axis of largest |d| (ties to the lowest axis); the next two cyclically,
+  // swapped when d[kz] < 0 to keep the winding
+  const float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
+  int kz = 0;
+  float m = ax;
+  if (ay > m) { kz = 1; m = ay; }
+  if (az > m) { kz = 2; }
+  int kx = kz == 2 ? 0 : kz + 1;
+  int ky = kx == 2 ? 0 : kx + 1;
+  const float dkz = sel3(r.dx, r.dy, r.dz, kz);
+  if (dkz < 0.0f) { const int t = kx; kx = ky; ky = t; }
+  r.kx = kx; r.ky = ky; r.kz = kz;
+  r.Sx = __fdiv_rn(sel3(r.dx, r.dy, r.dz, kx), dkz);
+  r.Sy = __fdiv_rn(sel3(r.dx, r.dy, r.dz, ky), dkz);
+  r.Sz = __fdiv_rn(1.0f, dkz);
+}
+
+// Conservative slab test of one box against [tmin, tlim]; returns the widened
+// entry distance in tn. Planes are chosen near/far by direction sign; NaNs
+// from 0*inf are ignored by fminf/fmaxf (the axis then does not cull).
+__device__ __forceinline__ bool slab(const Ray &r, float lox, float loy, float loz, float hix,
+                                     float hiy, float hiz, float tlim, float &tn) {
+  const float nx = r.nx ? hix : lox, fx = r.nx ? lox : hix;
+  const float ny = r.ny ? hiy : loy, fy = r.ny ? loy : hiy;
+  const float nz = r.nz ? hiz : loz, fz = r.nz ? loz : hiz;
+  const float t0x = fmaf(nx, r.rx, -r.orx), t1x = fmaf(fx, r.rx, -r.orx);
+  const float t0y = fmaf(ny, r.ry, -r.ory), t1y = fmaf(fy, r.ry, -r.ory);
+  const float t0z = fmaf(nz, r.rz, -r.orz), t1z = fmaf(fz, r.rz, -r.orz);
+  float a = fmaxf(fmaxf(t0x, t0y), t0z);
+  float b = fminf(fminf(t1x, t1y), t1z);
+  a = fmaf(-kTMargin, fabsf(a), a);
+  b = fmaf(kTMargin, fabsf(b), b);
+  a = fmaxf(a, r.tmin);
+  b = fminf(b, tlim);
+  tn = a;
+  return a <= b;
+}
+
+// Pinned watertight ray/triangle test (Woop, Benthin & Wald, JCGT 2(1) 2013;
+// the paper's App. G uses Moller-Trumbore instead). Steps and rounding:
+//   A = p0 - o, B = p1 - o, C = p2 - o; sheared Ax = fma(-Sx, A[kz], A[kx]),
+//   Ay = fma(-Sy, A[kz], A[ky]) (same for B, C); edge functions
+//   U = Cx*By - Cy*Bx, V = Ax*Cy - Ay*Cx, W = Bx*Ay - By*Ax with both
+//   products rounded (so a shared edge evaluates to exactly opposite values);
+//   if one is zero, all three are redone from exact double products; miss on
+//   mixed signs; det = (U+V)+W, miss if 0; T = fma(W, Cz, fma(V, Bz, U*Az))
+//   with Az = Sz*A[kz] etc.; t = T/det; accept iff tmin <= t <= tmax.
+// Returns t (and det, U for the barycentrics) on acceptance.
+__device__ __forceinline__ bool tri_test(const Ray &r, float4 p0, float4 p1, float4 p2,
+                                         float &t_out, float &V_out, float &W_out,
+                                         float &det_out) {
+  const float Akx = __fsub_rn(sel3(p0.x, p0.y, p0.z, r.kx), sel3(r.ox, r.oy, r.oz, r.kx));
+  const float Aky = __fsub_rn(sel3(p0.x, p0.y, p0.z, r.ky), sel3(r.ox, r.oy, r.oz, r.ky));
+  const float Akz = __fsub_rn(sel3(p0.x, p0.y, p0.z, r.kz), sel3(r.ox, r.oy, r.oz, r.kz));
+  const float Bkx = __fsub_rn(sel3(p1.x, p1.y, p1.z, r.kx), sel3(r.ox, r.oy, r.oz, r.kx));
+  const float Bky = __fsub_rn(sel3(p1.x, p1.y, p1.z, r.ky), sel3(r.ox, r.oy, r.oz, r.ky));
+  const float Bkz = __fsub_rn(sel3(p1.x, p1.y, p1.z, r.kz), sel3(r.ox, r.oy, r.oz, r.kz));
+  const float Ckx = __fsub_rn(sel3(p2.x, p2.y, p2.z, r.kx), sel3(r.ox, r.oy, r.oz, r.kx));
+  const float Cky = __fsub_rn(sel3(p2.x, p2.y, p2.z, r.ky), sel3(r.ox, r.oy, r.oz, r.ky));
+  const float Ckz = __fsub_rn(sel3(p2.x, p2.y, p2.z, r.kz), sel3(r.ox, r.oy, r.oz, r.kz));
+  const float Ax = fmaf(-r.Sx, Akz, Akx), Ay = fmaf(-r.Sy, Akz, Aky);
+  const float Bx = fmaf(-r.Sx, Bkz, Bkx), By = fmaf(-r.Sy, Bkz, Bky);
+  const float Cx = fmaf(-r.Sx, Ckz, Ckx), Cy = fmaf(-r.Sy, Ckz, Cky);
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.0f || V == 0.0f || W == 0.0f) {
+    U = __double2float_rn(__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx)));
+    V = __double2float_rn(__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx)));
+    W = __double2float_rn(__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax)));
+  }
+  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+  const float det = __fadd_rn(__fadd_rn(U, V), W);
+  if (det == 0.0f) return false;
+  const float Az = __fmul_rn(r.Sz, Akz), Bz = __fmul_rn(r.Sz, Bkz), Cz = __fmul_rn(r.Sz, Ckz);
+  const float T = fmaf(W, Cz, fmaf(V, Bz, __fmul_rn(U, Az)));
+  const float t = __fdiv_rn(T, det);
+  if (!(t >= r.tmin && t <= r.tmax)) return false;
+  t_out = t;
+  V_out = V;
+  W_out = W;
+  det_out = det;
+  return true;
+}
+
+// ------------------------------------------------------------------ loads
+__device__ __forceinline__ uint4 ldg4(const uint4 *p) { return __ldg(p); }
+__device__ __forceinline__ float4 ldg4f(const float4 *p) { return __ldg(p); }
+
+template <int NQ>
+__device__ __forceinline__ uint32_t qword(const uint4 (&q)[NQ], int i) {
+  const uint4 v = q[i >> 2];
+  switch (i & 3) {
+    case 0: return v.x;
+    case 1: return v.y;
+    case 2: return v.z;
+    default: return v.w;
+  }
+}
+
+// ------------------------------------------------------------------ stack
+struct Stack {
+  uint2 *sh;      // this thread's column in shared memory
+  int stride;     // blockDim.x
+  int cap_sh;     // entries in shared memory
+  int sp;
+  uint2 loc[kLocalStack];
+
+  __device__ __forceinline__ bool push(uint32_t ref, float tn) {
+    const uint2 e = make_uint2(ref, __float_as_uint(tn));
+    if (sp < cap_sh) sh[sp * stride] = e;
+    else if (sp < cap_sh + kLocalStack) loc[sp - cap_sh] = e;
+    else return false;
+    ++sp;
+    return true;
+  }
+  __device__ __forceinline__ uint2 pop() {
+    --sp;
+    return sp < cap_sh ? sh[sp * stride] : loc[sp - cap_sh];
+  }
+};
+
+// ------------------------------------------------------------------ leaf
+struct Best {
+  float t, u, v;
+  uint32_t id;
+};
+
+// Test the triangles [first, first + count). Closest: keep the lexicographic
+// minimum of (t, id). Any: return true at the first accepted hit.
+template <bool ANY>
+__device__ __forceinline__ bool visit_leaf(const TraceArgs &a, const Ray &r, uint32_t first,
+                                           uint32_t count, Best &b) {
+  for (uint32_t i = first; i < first + count; ++i) {
+    float4 p0, p1, p2;
+    uint32_t id;
+    if (a.prim_indirect) {
+      id = __ldg(a.prim_ids + i);
+      uint32_t i0, i1, i2;
+      if (a.tri_idx) {
+        i0 = __ldg(a.tri_idx + 3 * (size_t)id);
+        i1 = __ldg(a.tri_idx + 3 * (size_t)id + 1);
+        i2 = __ldg(a.tri_idx + 3 * (size_t)id + 2);
+      } else {
+        i0 = 3 * id; i1 = i0 + 1; i2 = i0 + 2;
+      }
+      p0 = ldg4f(a.verts + i0);
+      p1 = ldg4f(a.verts + i1);
+      p2 = ldg4f(a.verts + i2);
+    } else {
+      const float4 *q = a.prims + 3 * (size_t)i;
+      p0 = ldg4f(q);
+      p1 = ldg4f(q + 1);
+      p2 = ldg4f(q + 2);
+      id = __float_as_uint(p0.w);
+    }
+    float t, V, W, det;
+    if (!tri_test(r, p0, p1, p2, t, V, W, det)) continue;
+    if (ANY) return true;
+    if (t < b.t || (t == b.t && id < b.id)) {
+      b.t = t;
+      b.u = __fdiv_rn(V, det);
+      b.v = __fdiv_rn(W, det);
+      b.id = id;
+    }
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ wide node
+template <int W, int PREC, int SOA, int CREF>
+struct WideNode {
+  static constexpr int kHdr = PREC == PREC_U8 ? 16 : 0;
+  static constexpr int kElem = PREC == PREC_F32 ? 4 : (PREC == PREC_F16 ? 2 : 1);
+  static constexpr int kRefOff = kHdr + W * 6 * kElem;
+  static constexpr int kBytes = kRefOff + (CREF == REF_DIRECT ? 4 * W : 8 + W);
+  static constexpr int kStride = (kBytes + 31) & ~31;
+  static constexpr int NQ = (kBytes + 15) / 16;
+
+  static __device__ __forceinline__ int box_off(int k, int c) {
+    return kHdr + (SOA ? (c * W + k) : (k * 6 + c)) * kElem;
+  }
+  // raw quantity of coordinate c of child k (f32 value, f16 bits or u8 code)
+  static __device__ __forceinline__ uint32_t raw(const uint4 (&q)[NQ], int k, int c) {
+    const int off = box_off(k, c);
+    const uint32_t w = qword(q, off >> 2);
+    if (kElem == 4) return w;
+    if (kElem == 2) return (w >> ((off & 3) * 8)) & 0xFFFFu;
+    return (w >> ((off & 3) * 8)) & 0xFFu;
+  }
+};
+
+template <int W, int PREC, int SOA, int CREF, bool ANY>
+__device__ __forceinline__ bool trace_wide_ray(const TraceArgs &a, const Ray &r, Stack &st,
+                                               Best &b, uint32_t &err) {
+  using N = WideNode<W, PREC, SOA, CREF>;
+  uint32_t cur = a.root_ref;
+  uint32_t steps = 0;
+  st.sp = 0;
+  while (cur != kEmptyRef) {
+    if (++steps > a.max_steps) { err = kErrIter; return false; }
+    if (ref_is_interior(cur)) {
+      const uint4 *np = a.nodes + (size_t)ref_node(cur) * (N::kStride / 16);
+      uint4 q[N::NQ];
+#pragma unroll
+      for (int i = 0; i < N::NQ; ++i) q[i] = ldg4(np + i);
+      // u8 frame: coordinate = fma(code, 2^e, origin)
+      float ox = 0.f, oy = 0.f, oz = 0.f, sx = 1.f, sy = 1.f, sz = 1.f;
+      if (PREC == PREC_U8) {
+        ox = __uint_as_float(q[0].x); oy = __uint_as_float(q[0].y); oz = __uint_as_float(q[0].z);
+        sx = __uint_as_float((q[0].w & 0xFFu) << 23);
+        sy = __uint_as_float(((q[0].w >> 8) & 0xFFu) << 23);
+        sz = __uint_as_float(((q[0].w >> 16) & 0xFFu) << 23);
+      }
+      const float tlim = ANY ? r.tmax : fminf(r.tmax, b.t);
+      uint32_t cref[W];
+      float ctn[W];
+      uint32_t base_node = 0, base_prim = 0, leaf_acc = 0;
+      if (CREF == REF_INDIRECT) {
+        base_node = qword(q, N::kRefOff / 4);
+        base_prim = qword(q, N::kRefOff / 4 + 1);
+      }
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        uint32_t ref;
+        if (CREF == REF_DIRECT) {
+          ref = qword(q, N::kRefOff / 4 + k);
+        } else {
+          const uint32_t m = (qword(q, N::kRefOff / 4 + 2 + (k >> 2)) >> ((k & 3) * 8)) & 0xFFu;
+          if (m == 0) ref = kEmptyRef;
+          else if (m & kMetaInterior) ref = ref_interior(base_node + (m & 0x7Fu));
+          else { ref = ref_leaf(base_prim + leaf_acc, m); leaf_acc += m; }
+        }
+        float lo[3], hi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const uint32_t ql = N::raw(q, k, c), qh = N::raw(q, k, c + 3);
+          if (PREC == PREC_F32) {
+            lo[c] = __uint_as_float(ql);
+            hi[c] = __uint_as_float(qh);
+          } else if (PREC == PREC_F16) {
+            lo[c] = __half2float(__ushort_as_half((unsigned short)ql));
+            hi[c] = __half2float(__ushort_as_half((unsigned short)qh));
+          } else {
+            const float o = c == 0 ? ox : (c == 1 ? oy : oz);
+            const float s = c == 0 ? sx : (c == 1 ? sy : sz);
+            lo[c] = fmaf((float)ql, s, o);
+            hi[c] = fmaf((float)qh, s, o);
+          }
+        }
+        float tn;
+        const bool hit = slab(r, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], tlim, tn) && ref != kEmptyRef;
+        cref[k] = hit ? ref : kEmptyRef;
+        ctn[k] = hit ? tn : __int_as_float(0x7f800000);
+      }
+      if (!ANY && a.ordered) {
+        // ascending entry distance (odd-even transposition network)
+#pragma unroll
+        for (int pass = 0; pass < W; ++pass) {
+#pragma unroll
+          for (int k = pass & 1; k + 1 < W; k += 2) {
+            const bool sw = ctn[k + 1] < ctn[k];
+            const float t0 = sw ? ctn[k + 1] : ctn[k], t1 = sw ? ctn[k] : ctn[k + 1];
+            const uint32_t r0 = sw ? cref[k + 1] : cref[k], r1 = sw ? cref[k] : cref[k + 1];
+            ctn[k] = t0; ctn[k + 1] = t1; cref[k] = r0; cref[k + 1] = r1;
+          }
+        }
+      }
+      // push every hit child but the first, last one first; go on with the first
+      uint32_t next = kEmptyRef;
+      float next_tn = 0.f;
+#pragma unroll
+      for (int k = W - 1; k >= 0; --k) {
+        if (cref[k] == kEmptyRef) continue;
+        if (next != kEmptyRef && !st.push(next, next_tn)) { err = kErrStack; return false; }
+        next = cref[k];
+        next_tn = ctn[k];
+      }
+      if (next != kEmptyRef) { cur = next; continue; }
+    } else {
+      if (visit_leaf<ANY>(a, r, ref_leaf_first(cur), ref_leaf_count(cur), b)) return true;
+    }
+    // next stacked entry that can still hold a closer hit
+    cur = kEmptyRef;
+    while (st.sp > 0) {
+      const uint2 e = st.pop();
+      if (ANY || __uint_as_float(e.y) <= b.t) { cur = e.x; break; }
+    }
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ own-box node
+template <int SOA, int CREF, bool ANY>
+__device__ __forceinline__ bool trace_bin_ray(const TraceArgs &a, const Ray &r, Stack &st,
+                                              Best &b, uint32_t &err) {
+  if (a.n_nodes == 0) return false;
+  uint32_t cur = 0;
+  uint32_t steps = 0;
+  st.sp = 0;
+  while (cur != kEmptyRef) {
+    if (++steps > a.max_steps) { err = kErrIter; return false; }
+    float lo0, lo1, lo2, hi0, hi1, hi2;
+    uint32_t ref, meta;
+    if (SOA) {
+      const uint2 *bp = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(a.nodes) +
+                                                        (size_t)cur * kBinBoxBytes);
+      const uint2 b0 = __ldg(bp), b1 = __ldg(bp + 1), b2 = __ldg(bp + 2);
+      const uint2 rm = __ldg(a.nodes2 + cur);
+      lo0 = __uint_as_float(b0.x); lo1 = __uint_as_float(b0.y); lo2 = __uint_as_float(b1.x);
+      hi0 = __uint_as_float(b1.y); hi1 = __uint_as_float(b2.x); hi2 = __uint_as_float(b2.y);
+      ref = rm.x; meta = rm.y;
+    } else {
+      const uint4 q0 = ldg4(a.nodes + 2 * (size_t)cur), q1 = ldg4(a.nodes + 2 * (size_t)cur + 1);
+      lo0 = __uint_as_float(q0.x); lo1 = __uint_as_float(q0.y); lo2 = __uint_as_float(q0.z);
+      hi0 = __uint_as_float(q0.w); hi1 = __uint_as_float(q1.x); hi2 = __uint_as_float(q1.y);
+      ref = q1.z; meta = q1.w;
+    }
+    const float tlim = ANY ? r.tmax : fminf(r.tmax, b.t);
+    float tn;
+    if (slab(r, lo0, lo1, lo2, hi0, hi1, hi2, tlim, tn)) {
+      const uint32_t cnt = bin_meta_count(meta);
+      if (cnt > 0) {
+        if (visit_leaf<ANY>(a, r, ref, cnt, b)) return true;
+      } else {
+        const uint32_t l = CREF == REF_DIRECT ? cur + 1 : ref;
+        const uint32_t rr = CREF == REF_DIRECT ? cur + ref : ref + 1;
+        const uint32_t ax = bin_meta_axis(meta);
+        const bool neg = ax == 0 ? r.nx : (ax == 1 ? r.ny : r.nz);
+        const bool swap = !ANY && a.ordered && neg;
+        if (!st.push(swap ? l : rr, 0.0f)) { err = kErrStack; return false; }
+        cur = swap ? rr : l;
+        continue;
+      }
+    }
+    cur = st.sp > 0 ? st.pop().x : kEmptyRef;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ kernel body
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY>
+__device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
+  extern __shared__ uint2 smem_stack[];
+  Stack st;
+  st.sh = smem_stack + threadIdx.x;
+  st.stride = blockDim.x;
+  st.cap_sh = (int)a.smem_stack;
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.work, 32ull);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base >= a.n) break;
+    const unsigned long long rid = base + lane;
+    if (rid < a.n) {
+      Ray r;
+      setup_ray(ldg4f(a.rays + 2 * rid), ldg4f(a.rays + 2 * rid + 1), r);
+      Best b{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_MISS};
+      uint32_t err = 0;
+      bool found = false;
+      if constexpr (OWN) {
+        found = trace_bin_ray<SOA, CREF, ANY>(a, r, st, b, err);
+      } else {
+        if (a.root_ref != kEmptyRef) found = trace_wide_ray<W, PREC, SOA, CREF, ANY>(a, r, st, b, err);
+      }
+      if (err) atomicCAS(a.status, 0u, err);
+      if (ANY) {
+        static_cast<uint32_t *>(a.out)[rid] = err ? SCION_PRIM_ERROR : (found ? 1u : 0u);
+      } else {
+        if (err) b = Best{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_ERROR};
+        static_cast<uint4 *>(a.out)[rid] =
+            make_uint4(__float_as_uint(b.t), __float_as_uint(b.u), __float_as_uint(b.v), b.id);
+      }
+    }
+  }
+  // the last CTA to finish resets the counters for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t prev = atomicAdd(a.exit_count, 1u);
+    if (prev == gridDim.x - 1) {
+      *a.work = 0ull;
+      *a.exit_count = 0u;
+      __threadfence();
+    }
+  }
+}
+
+}  // namespace scion

@@ -1,0 +1,35 @@
+// Instantiates the traversal kernels of one node family. Compiled several
+// times with -DSCION_OWN=1, or -DSCION_W=<2|4|8> -DSCION_PREC=<0|1|2>, so the
+// families build in parallel.
+#include "kernels.h"
+
+#define SCION_CAT_(a, b) a##b
+#define SCION_CAT(a, b) SCION_CAT_(a, b)
+
+namespace scion {
+
+#if defined(SCION_OWN)
+#define SCION_FAMILY_OWN true
+#define SCION_W 2
+#define SCION_PREC 0
+#define SCION_GETTER kernels_own
+#else
+#define SCION_FAMILY_OWN false
+#define SCION_GETTER SCION_CAT(SCION_CAT(SCION_CAT(kernels_w, SCION_W), _p), SCION_PREC)
+#endif
+
+template <int SOA, int CREF, bool ANY>
+__global__ void __launch_bounds__(kMaxThreadsPerBlock) trace_kernel(TraceArgs a) {
+  trace_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, ANY>(a);
+}
+
+TraceKernel SCION_GETTER(int soa, int cref, int any) {
+  static const TraceKernel table[2][2][2] = {
+      {{trace_kernel<0, 0, false>, trace_kernel<0, 0, true>},
+       {trace_kernel<0, 1, false>, trace_kernel<0, 1, true>}},
+      {{trace_kernel<1, 0, false>, trace_kernel<1, 0, true>},
+       {trace_kernel<1, 1, false>, trace_kernel<1, 1, true>}}};
+  return table[soa & 1][cref & 1][any & 1];
+}
+
+}  // namespace scion

@@ -1,0 +1,303 @@
+"""Python binding of the scion C ABI (include/scion.h, include/scion_debug.h).
+
+Argument marshalling only: every step of build, packing and traversal runs in
+the native library ``_build/libscion.so`` (host C++ builder, CUDA kernels for
+sm_103a). PyTorch provides device memory and streams. There is no fallback:
+if the library is missing or fails to load, every call raises.
+
+The functions carry the C names: ``scion_build``, ``scion_bvh_info``,
+``scion_trace_closest``, ``scion_trace_any``, ``scion_get_status``,
+``scion_destroy``, plus the host-only ``scion_debug_*`` introspection calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libscion.so")
+
+SCION_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_LAYOUT", 3: "OOM", 4: "CUDA",
+                5: "STACK_OVERFLOW", 6: "ITER_LIMIT", 7: "BAD_INPUT"}
+PRIM_MISS = 0xFFFFFFFF
+PRIM_ERROR = 0xFFFFFFFE
+
+
+class ScionError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)} ({last_error()})")
+
+
+class LayoutDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "width", "box_layout", "box_prec", "child_ref", "prim_ref", "order", "leaf_max",
+        "sah_bins", "treelet_bytes", "reserved")]
+
+
+class TraceParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "threads_per_block", "ctas_per_sm", "reg_stack", "smem_stack", "ordered_children",
+        "rays_per_fetch", "max_steps", "reserved")]
+
+
+class DebugInfo(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_uint32), ("node_stride", ctypes.c_uint32),
+                ("n_leaf_entries", ctypes.c_uint32), ("root_ref", ctypes.c_uint32),
+                ("depth", ctypes.c_uint32), ("stack_need", ctypes.c_uint32),
+                ("own_box", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("node_bytes", ctypes.c_uint64), ("prim_bytes", ctypes.c_uint64),
+                ("vert_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
+
+
+PREC = {"f32": 0, "f16": 1, "u8": 2}
+ORDER = {"dfs": 0, "bfs": 1, "treelet": 2}
+
+
+def layout(width=2, box_layout="aos", box_prec="f32", child_ref="direct", prim_ref="indirect",
+           order="dfs", leaf_max=4, sah_bins=16, treelet_bytes=1024) -> LayoutDesc:
+    """A layout descriptor from readable names."""
+    return LayoutDesc(width, 0 if box_layout == "aos" else 1, PREC[box_prec],
+                      0 if child_ref == "direct" else 1, 0 if prim_ref == "direct" else 1,
+                      ORDER[order], leaf_max, sah_bins, treelet_bytes, 0)
+
+
+# The four node layouts swept on the coherent/incoherent workloads, each with
+# direct and indirect triangle storage.
+SWEEP = {
+    "bvh2_aos_f32": dict(width=2, box_layout="aos", box_prec="f32"),
+    "bvh4_soa_f32": dict(width=4, box_layout="soa", box_prec="f32"),
+    "bvh8_soa_f16": dict(width=8, box_layout="soa", box_prec="f16"),
+    "bvh8_aos_u8": dict(width=8, box_layout="aos", box_prec="u8"),
+}
+
+
+def sweep_layouts():
+    out = {}
+    for name, kw in SWEEP.items():
+        for pr in ("direct", "indirect"):
+            out[f"{name}_{pr}"] = layout(prim_ref=pr, **kw)
+    return out
+
+
+_lib = None
+
+
+def lib():
+    """Load the native library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"native library missing: {LIB_PATH}; run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        L.scion_build.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), P, ctypes.POINTER(P)]
+        L.scion_bvh_info.argtypes = [P, P, P, P, P]
+        L.scion_trace_closest.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
+        L.scion_trace_any.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
+        L.scion_get_status.argtypes = [P, P, P]
+        L.scion_destroy.argtypes = [P]
+        L.scion_destroy.restype = None
+        L.scion_status_string.argtypes = [I]
+        L.scion_status_string.restype = ctypes.c_char_p
+        L.scion_last_error.restype = ctypes.c_char_p
+        L.scion_debug_build_host.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), ctypes.POINTER(P)]
+        L.scion_debug_host_stats.argtypes = [P, ctypes.POINTER(DebugInfo)]
+        L.scion_debug_host_decode.argtypes = [P, P, P, P, P, P, P]
+        L.scion_debug_host_destroy.argtypes = [P]
+        L.scion_debug_host_destroy.restype = None
+        L.scion_debug_f16_round.argtypes = [ctypes.c_float, I]
+        L.scion_debug_f16_round.restype = U32
+        L.scion_debug_f16_decode.argtypes = [U32]
+        L.scion_debug_f16_decode.restype = ctypes.c_float
+        for name in ("scion_build", "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
+                     "scion_get_status", "scion_debug_build_host", "scion_debug_host_stats",
+                     "scion_debug_host_decode"):
+            getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    try:
+        return lib().scion_last_error().decode()
+    except Exception:  # noqa: BLE001 - message helper only
+        return ""
+
+
+def _check(st: int, what: str):
+    if st != SCION_OK:
+        raise ScionError(st, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class BVH:
+    """Owning handle of a device BVH (scion_bvh)."""
+
+    def __init__(self, handle, n_tris: int, n_verts: int, desc: LayoutDesc):
+        self.handle = handle
+        self.n_tris = n_tris
+        self.n_verts = n_verts
+        self.desc = desc
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.scion_destroy(self.handle)
+            self.handle = None
+
+    def info(self):
+        return scion_bvh_info(self)
+
+
+def _as_np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def scion_build(verts, desc: LayoutDesc, indices=None, stream=None) -> BVH:
+    """Build a BVH from float32 vertices [n_verts, 3] (numpy or torch, host or
+    device) and optional uint32 indices [n_tris, 3]."""
+    import torch
+    keep = []
+
+    def ptr(x, dtype):
+        if x is None:
+            return None, 0
+        if isinstance(x, torch.Tensor):
+            t = x.contiguous()
+            keep.append(t)
+            return ctypes.c_void_p(t.data_ptr()), t.shape[0]
+        a = _as_np(x, dtype)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.c_void_p), a.shape[0]
+
+    vp, nv = ptr(verts, np.float32)
+    ip, nt = ptr(indices, np.uint32)
+    if indices is None:
+        nt = nv // 3
+    h = ctypes.c_void_p()
+    _check(lib().scion_build(vp, nv, ip, nt, ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(h)),
+           "scion_build")
+    return BVH(h, nt, nv, desc)
+
+
+def scion_bvh_info(bvh: BVH) -> dict:
+    nb, pb = ctypes.c_uint64(), ctypes.c_uint64()
+    d, n = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().scion_bvh_info(bvh.handle, ctypes.byref(nb), ctypes.byref(pb), ctypes.byref(d),
+                                ctypes.byref(n)), "scion_bvh_info")
+    return {"node_bytes": nb.value, "prim_bytes": pb.value, "depth": d.value, "n_nodes": n.value}
+
+
+def _params(params):
+    if params is None:
+        return None
+    if isinstance(params, TraceParams):
+        return ctypes.byref(params)
+    return ctypes.byref(TraceParams(**params))
+
+
+def scion_trace_closest(bvh: BVH, rays, hits=None, params=None, stream=None):
+    """Closest hits of device rays (float32 [n, 8]); returns int32 [n, 4]
+    holding (t, u, v) as float bits and prim as uint32 bits."""
+    import torch
+    assert rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous()
+    n = rays.shape[0]
+    if hits is None:
+        hits = torch.empty((n, 4), dtype=torch.int32, device=rays.device)
+    _check(lib().scion_trace_closest(bvh.handle, ctypes.c_void_p(rays.data_ptr()), n,
+                                     ctypes.c_void_p(hits.data_ptr()), _params(params),
+                                     _stream_ptr(stream)), "scion_trace_closest")
+    return hits
+
+
+def scion_trace_any(bvh: BVH, rays, occluded=None, params=None, stream=None):
+    """Any-hit flags (int32 [n]: 1 occluded, 0 clear) of device rays."""
+    import torch
+    assert rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous()
+    n = rays.shape[0]
+    if occluded is None:
+        occluded = torch.empty((n,), dtype=torch.int32, device=rays.device)
+    _check(lib().scion_trace_any(bvh.handle, ctypes.c_void_p(rays.data_ptr()), n,
+                                 ctypes.c_void_p(occluded.data_ptr()), _params(params),
+                                 _stream_ptr(stream)), "scion_trace_any")
+    return occluded
+
+
+def scion_get_status(bvh: BVH, stream=None) -> int:
+    st = ctypes.c_int()
+    _check(lib().scion_get_status(bvh.handle, _stream_ptr(stream), ctypes.byref(st)), "scion_get_status")
+    return st.value
+
+
+def scion_destroy(bvh: BVH):
+    if bvh.handle:
+        lib().scion_destroy(bvh.handle)
+        bvh.handle = None
+
+
+def split_hits(hits_i32) -> np.ndarray:
+    """Host structured array (t, u, v float32; prim uint32) from trace output."""
+    h = hits_i32.cpu().numpy() if hasattr(hits_i32, "cpu") else np.asarray(hits_i32)
+    out = np.empty(h.shape[0], dtype=[("t", np.float32), ("u", np.float32), ("v", np.float32),
+                                      ("prim", np.uint32)])
+    out.view(np.int32).reshape(-1, 4)[:] = h
+    return out
+
+
+# ------------------------------------------------------------- host debug ABI
+@dataclass
+class HostDecode:
+    info: dict
+    kind: np.ndarray
+    a: np.ndarray
+    c: np.ndarray
+    boxes: np.ndarray
+    own_boxes: np.ndarray
+    leaf_ids: np.ndarray
+
+
+def scion_debug_build_host(verts, desc: LayoutDesc, indices=None) -> HostDecode:
+    """Pack on the host only and decode every node (no GPU involved)."""
+    v = _as_np(verts, np.float32)
+    ix = None if indices is None else _as_np(indices, np.uint32)
+    nt = v.shape[0] // 3 if ix is None else ix.shape[0]
+    h = ctypes.c_void_p()
+    _check(lib().scion_debug_build_host(v.ctypes.data_as(ctypes.c_void_p), v.shape[0],
+                                        None if ix is None else ix.ctypes.data_as(ctypes.c_void_p),
+                                        nt, ctypes.byref(desc), ctypes.byref(h)), "scion_debug_build_host")
+    try:
+        inf = DebugInfo()
+        _check(lib().scion_debug_host_stats(h, ctypes.byref(inf)), "scion_debug_host_stats")
+        info = {k: getattr(inf, k) for k, _ in DebugInfo._fields_}
+        nn = inf.n_nodes
+        kind = np.zeros(nn * 8, np.uint32)
+        a = np.zeros(nn * 8, np.uint32)
+        c = np.zeros(nn * 8, np.uint32)
+        boxes = np.zeros(nn * 8 * 6, np.float32)
+        own = np.zeros(nn * 6, np.float32)
+        ids = np.zeros(max(inf.n_leaf_entries, 1), np.uint32)
+        P = lambda x: x.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        _check(lib().scion_debug_host_decode(h, P(kind), P(a), P(c), P(boxes), P(own), P(ids)),
+               "scion_debug_host_decode")
+    finally:
+        lib().scion_debug_host_destroy(h)
+    return HostDecode(info, kind.reshape(nn, 8), a.reshape(nn, 8), c.reshape(nn, 8),
+                      boxes.reshape(nn, 8, 6), own.reshape(nn, 6), ids[:inf.n_leaf_entries])
+
+
+def scion_debug_f16_round(x: float, direction: int) -> int:
+    return int(lib().scion_debug_f16_round(float(x), int(direction)))
+
+
+def scion_debug_f16_decode(h: int) -> float:
+    return float(lib().scion_debug_f16_decode(int(h)))

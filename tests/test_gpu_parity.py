@@ -1,0 +1,217 @@
+"""GPU parity: every layout's closest-hit and any-hit results match the CPU
+oracle bit for bit (hit/miss, prim, t, u, v), through the C ABI."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_15028_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sc_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_15028_gb300 import build as b
+    b.build()
+    from paper_2511_15028_gb300 import scion
+    scion.lib()
+    return scion
+
+
+def gpu_closest(scion, bvh, rays, params=None):
+    r = torch.from_numpy(np.ascontiguousarray(rays, np.float32)).cuda()
+    h = scion.scion_trace_closest(bvh, r, params=params)
+    torch.cuda.synchronize()
+    return scion.split_hits(h)
+
+
+def gpu_any(scion, bvh, rays, params=None):
+    r = torch.from_numpy(np.ascontiguousarray(rays, np.float32)).cuda()
+    o = scion.scion_trace_any(bvh, r, params=params)
+    torch.cuda.synchronize()
+    return o.cpu().numpy().astype(np.uint32)
+
+
+def assert_same_hits(got, exp, what=""):
+    g = got.view(np.uint32).reshape(-1, 4)
+    e = np.ascontiguousarray(exp).view(np.uint32).reshape(-1, 4)
+    bad = np.where(np.any(g != e, axis=1))[0]
+    assert bad.size == 0, f"{what}: {bad.size} mismatches, first {bad[:5]}: gpu {got[bad[:3]]} oracle {exp[bad[:3]]}"
+
+
+ALL = []
+for w, lay, prec, cref, pref, order in itertools.product(
+        (2, 4, 8), ("aos", "soa"), ("f32", "f16", "u8"), ("direct", "indirect"),
+        ("direct", "indirect"), ("dfs", "bfs", "treelet")):
+    if w == 2 and prec == "f32" and cref == "direct" and order != "dfs":
+        continue
+    ALL.append(dict(width=w, box_layout=lay, box_prec=prec, child_ref=cref, prim_ref=pref, order=order))
+
+
+@pytest.fixture(scope="module")
+def config1(oracle_mod):
+    sc = scenes.config1_scene()
+    rays = scenes.config1_rays()
+    tris = sc.triangles()
+    exp = oracle_mod.closest_brute(tris, rays)
+    occ = oracle_mod.any_brute(tris, rays)
+    return sc, rays, exp, occ
+
+
+@pytest.mark.parametrize("kw", ALL, ids=lambda kw: "-".join(str(v) for v in kw.values()))
+def test_config1_every_layout_bit_exact(sc_mod, config1, kw):
+    sc, rays, exp, occ = config1
+    bvh = sc_mod.scion_build(sc.verts, sc_mod.layout(**kw), sc.indices)
+    got = gpu_closest(sc_mod, bvh, rays)
+    assert_same_hits(got, exp, str(kw))
+    assert np.array_equal(gpu_any(sc_mod, bvh, rays), occ)
+    unordered = gpu_closest(sc_mod, bvh, rays, params=dict(ordered_children=2))
+    assert_same_hits(unordered, exp, "unordered")
+    assert sc_mod.scion_get_status(bvh) == 0
+
+
+def test_closed_form_scenes_on_gpu(sc_mod, oracle_mod):
+    tri = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    quad = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 0, 0], [1, 1, 0], [0, 1, 0]], np.float32)
+    rays = []
+    for x, y in ((0.25, 0.5), (0.0, 0.0), (1.0, 0.0), (0.5, 0.5), (0.75, 0.5), (0.25, 0.25)):
+        rays.append([x, y, 1, 1e-4, 0, 0, -1, np.inf])
+    rays += [[0.25, 0.5, 1, 1, 0, 0, -1, np.inf], [0.25, 0.5, 1, 1e-4, 0, 0, -1, 1],
+             [0.25, 0.5, 1, 1e-4, 0, 0, -1, 0.5], [0.25, 0.5, 1, 2, 0, 0, -1, 1],
+             [0.25, 0.5, 1, 1e-4, 0, 0, 0, np.inf], [0.25, 0.5, 1, 1e-4, 1, 0, 0, np.inf],
+             [0.25, 0.5, -1, 1e-4, 0, 0, 1, np.inf], [0.25, 0.5, 1, 1e-4, 0, 0, 1, np.inf]]
+    rays = np.array(rays, np.float32)
+    for verts in (tri, quad):
+        for kw in ALL[::7]:
+            bvh = sc_mod.scion_build(verts, sc_mod.layout(**kw))
+            exp = oracle_mod.closest_brute(verts.reshape(-1, 9), rays)
+            assert_same_hits(gpu_closest(sc_mod, bvh, rays), exp, str(kw))
+            assert np.array_equal(gpu_any(sc_mod, bvh, rays), oracle_mod.any_brute(verts.reshape(-1, 9), rays))
+
+
+def test_ties_duplicates_and_stack_of_quads(sc_mod, oracle_mod):
+    rng = np.random.default_rng(11)
+    quads = []
+    for k in range(100):
+        z = k / 8.0
+        quads += [[0, 0, z], [1, 0, z], [1, 1, z], [0, 0, z], [1, 1, z], [0, 1, z]]
+    verts = np.array(quads, np.float32).reshape(-1, 9)[rng.permutation(200)].reshape(-1, 3)
+    dup = np.repeat(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)[None], 9, 0).reshape(-1, 3)
+    o = np.stack([rng.integers(1, 64, 4096) / 64.0, rng.integers(1, 64, 4096) / 64.0, np.full(4096, 20.0)], -1)
+    rays = scenes.make_rays(o.astype(np.float32), np.tile(np.float32([[0, 0, -1]]), (4096, 1)), 1e-4, np.inf)
+    diag = rays.copy()
+    diag[:, 1] = diag[:, 0]  # exactly on the quads' shared diagonal: ties
+    for v in (verts, dup):
+        for kw in ALL[::5]:
+            bvh = sc_mod.scion_build(v, sc_mod.layout(**kw))
+            for rr in (rays, diag):
+                assert_same_hits(gpu_closest(sc_mod, bvh, rr), oracle_mod.closest_brute(v.reshape(-1, 9), rr), str(kw))
+
+
+def test_edge_cases(sc_mod, oracle_mod):
+    sc = scenes.config1_scene()
+    rays = scenes.config1_rays()
+    bvh = sc_mod.scion_build(sc.verts, sc_mod.layout())
+    # n = 0 is a no-op
+    empty = torch.zeros((0, 8), dtype=torch.float32, device="cuda")
+    assert sc_mod.scion_trace_closest(bvh, empty).shape == (0, 4)
+    # degenerate rays: zero direction, NaN origin, tmin > tmax, axis-parallel
+    bad = rays[:64].copy()
+    bad[0, 4:7] = 0
+    bad[1, 0] = np.nan
+    bad[2, 3], bad[2, 7] = 5.0, 1.0
+    bad[3, 4:7] = [0, 0, -1]
+    bad[4, 4:7] = [0, 0, 1]
+    bad[5, 4:7] = [1, 0, 0]
+    bad[6, 0:3] = [0.0, 0.0, 0.5]
+    bad[6, 4:7] = [0, -1, 0]
+    exp = oracle_mod.closest_brute(sc.triangles(), bad)
+    for kw in ALL[::3]:
+        b = sc_mod.scion_build(sc.verts, sc_mod.layout(**kw), sc.indices)
+        assert_same_hits(gpu_closest(sc_mod, b, bad), exp, str(kw))
+    # scenes with no hittable triangle, and a scene with non-finite triangles
+    none = np.full((9, 3), np.nan, np.float32)
+    for kw in ({}, dict(width=8, box_prec="u8")):
+        b = sc_mod.scion_build(none, sc_mod.layout(**kw))
+        got = gpu_closest(sc_mod, b, rays[:100])
+        assert np.all(got["prim"] == 0xFFFFFFFF) and np.all(np.isinf(got["t"]))
+        assert np.all(gpu_any(sc_mod, b, rays[:100]) == 0)
+    v = sc.triangles().reshape(-1, 3).copy()
+    v[7] = np.inf
+    v[300] = np.nan
+    b = sc_mod.scion_build(v, sc_mod.layout(width=4))
+    assert_same_hits(gpu_closest(sc_mod, b, rays), oracle_mod.closest_brute(v.reshape(-1, 9), rays), "nonfinite")
+
+
+def test_device_errors_are_reported_not_faulted(sc_mod):
+    """A tiny step limit and a stack deeper than the traversal stack end the
+    affected rays with prim = ERROR and a status code; nothing faults."""
+    sc = scenes.config1_scene()
+    rays = scenes.config1_rays()
+    bvh = sc_mod.scion_build(sc.verts, sc_mod.layout(), sc.indices)
+    got = gpu_closest(sc_mod, bvh, rays, params=dict(max_steps=1))
+    assert np.any(got["prim"] == 0xFFFFFFFE)
+    assert sc_mod.scion_get_status(bvh) == 6
+    assert sc_mod.scion_get_status(bvh) == 0  # cleared
+    # a chain: triangles at x = 4^k (k = -50..49) whose two-bin SAH tree peels
+    # one triangle per level (depth 100); a ray along +x through all of them
+    # pushes one far child per level, more than the 64-entry stack holds
+    n = 100
+    c = 4.0 ** (np.arange(n) - n // 2)
+    s = c / 2
+    v = np.zeros((n, 3, 3))
+    v[:, 0] = np.stack([c, -s, -s], -1)
+    v[:, 1] = np.stack([c, s, -s], -1)
+    v[:, 2] = np.stack([c, 0 * s, 2 * s], -1)
+    v = v.astype(np.float32).reshape(-1, 3)
+    desc = sc_mod.layout(leaf_max=1, sah_bins=2)
+    assert sc_mod.scion_debug_build_host(v, desc).info["depth"] == n
+    b = sc_mod.scion_build(v, desc)
+    ray = np.array([[-1.0, 0.0, 0.0, 0.0, 1, 0, 0, np.inf]], np.float32)
+    got = gpu_closest(sc_mod, b, ray)
+    assert got["prim"][0] == 0xFFFFFFFE
+    assert sc_mod.scion_get_status(b) == 5
+    # a short ray that ends before the deep part is unaffected
+    ok = gpu_any(sc_mod, b, np.array([[-1.0, 0.0, 0.0, 0.0, -1, 0, 0, np.inf]], np.float32))
+    assert ok[0] == 0 and sc_mod.scion_get_status(b) == 0
+
+
+def test_config2_reduced_all_ray_kinds(sc_mod, oracle_mod):
+    """Scaled-down coherent + incoherent workload (height field + spheres):
+    primary, one diffuse bounce, shadow rays; all eight swept layouts."""
+    sc = scenes.config2_scene(side=181, n_spheres=64)
+    tris = sc.triangles()
+    prim = scenes.config2_primary(320, 180)
+    ob = oracle_mod.BVH2(tris)
+    h = ob.closest(prim)
+    bounce = scenes.bounce_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"], seed=21)
+    shadow = scenes.shadow_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"])
+    eb = ob.closest(bounce)
+    es = ob.any(shadow)
+    for name, d in sc_mod.sweep_layouts().items():
+        bvh = sc_mod.scion_build(sc.verts, d, sc.indices)
+        assert_same_hits(gpu_closest(sc_mod, bvh, prim), h, name + " primary")
+        assert_same_hits(gpu_closest(sc_mod, bvh, bounce), eb, name + " bounce")
+        assert np.array_equal(gpu_any(sc_mod, bvh, shadow), es), name + " shadow"
+
+
+def test_random_soup_incoherent(sc_mod, oracle_mod):
+    rng = scenes.rng_for(31)
+    n = 1 << 17
+    verts = scenes.random_soup(rng, n, mu=math.log(0.002 * math.sqrt((1 << 23) / n)))
+    tris = verts.reshape(-1, 9)
+    rays = scenes.random_rays(rng, 1 << 15, (0, 0, 0), (1, 1, 1))
+    short = rays.copy()
+    short[:, 7] = 0.05
+    ob = oracle_mod.BVH2(tris)
+    exp = ob.closest(rays)
+    eocc = ob.any(short)
+    for name, d in sc_mod.sweep_layouts().items():
+        bvh = sc_mod.scion_build(verts, d)
+        assert_same_hits(gpu_closest(sc_mod, bvh, rays), exp, name)
+        assert np.array_equal(gpu_any(sc_mod, bvh, short), eocc), name
