@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark: closest-hit / any-hit traversal throughput per layout.
+
+Workload (one step): the coherent + incoherent scene of 1,373,138 triangles
+(724 x 724 fBm height field + 256 icospheres), 1920 x 1080 primary camera rays
+(closest hit), one cosine-weighted diffuse bounce ray per primary hit (closest
+hit) and one shadow ray per primary hit toward a point light (any hit), all
+inputs resident in HBM. Every one of the eight swept layouts is timed; the
+headline value is the best layout's whole-step Mrays/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank traces its own copy
+of the workload (weak scaling) and the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "closest-hit Mrays/s & BVH MB per layout; % BW roofline; batched/bwd vs plain"
+WORKLOAD = ("coherent+incoherent: fBm 724x724 height field + 256 icospheres (1,373,138 tris); "
+            "1920x1080 primary (closest) + 1 diffuse bounce per hit (closest) + 1 shadow per hit (any)")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def trimmed_mean(xs):
+    """Paper's protocol (Section 9.1): of 9 runs drop the 2 lowest and 2
+    highest and average the rest; for other counts trim 2/9 on each side."""
+    xs = sorted(xs)
+    k = int(round(len(xs) * 2 / 9)) if len(xs) >= 5 else 0
+    core = xs[k:len(xs) - k] if len(xs) > 2 * k else xs
+    return float(sum(core) / len(core))
+
+
+# ------------------------------------------------------------------ algorithmic bytes
+def node_load_bytes(desc) -> int:
+    """Bytes one node visit loads (128-bit loads of the used part of a node)."""
+    w, prec, cref = desc.width, desc.box_prec, desc.child_ref
+    if w == 2 and prec == 0:
+        return 32
+    elem = {0: 4, 1: 2, 2: 1}[prec]
+    used = (16 if prec == 2 else 0) + w * 6 * elem + (4 * w if cref == 0 else 8 + w)
+    return (used + 15) // 16 * 16
+
+
+def tri_load_bytes(desc, indexed: bool) -> int:
+    if desc.prim_ref == 0:
+        return 48
+    return 4 + (12 if indexed else 0) + 48
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = os.path.join("/tmp", f"scion_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            if self.bus_id and self.bus_id.lower()[-12:] not in f[1].lower():
+                continue
+            rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(scion, torch, dev, primary_desc):
+    from paper_2511_15028_gb300 import scenes
+    sc = scenes.config2_scene()
+    prim = scenes.config2_primary()
+    bvh = scion.scion_build(sc.verts, primary_desc, sc.indices)
+    d_prim = torch.from_numpy(prim).to(dev)
+    h = scion.split_hits(scion.scion_trace_closest(bvh, d_prim))
+    bounce = scenes.bounce_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"], seed=2002)
+    shadow = scenes.shadow_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"])
+    return sc, prim, bounce, shadow
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler=None):
+    """K timed steps of (primary closest, bounce closest, shadow any); events
+    on the launching stream around each launch."""
+    d_p, d_b, d_s = rays
+    o_p, o_b, o_s = outs
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        scion.scion_trace_closest(bvh, d_p, o_p)
+        scion.scion_trace_closest(bvh, d_b, o_b)
+        scion.scion_trace_any(bvh, d_s, o_s)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    if sampler:
+        sampler.start()
+    for k in range(steps):
+        flush_l2(flush_buf)
+        e = ev[k]
+        e[0].record(stream)
+        scion.scion_trace_closest(bvh, d_p, o_p)
+        e[1].record(stream)
+        scion.scion_trace_closest(bvh, d_b, o_b)
+        e[2].record(stream)
+        scion.scion_trace_any(bvh, d_s, o_s)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in ev])  # ms
+    step = per.sum(axis=1)
+    return step, per, clocks
+
+
+def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf):
+    """The same step through the public API from pinned host buffers: every
+    step copies its rays host->device, traces, and reads the results back."""
+    dev = torch.device("cuda")
+    h_in = [torch.from_numpy(r).pin_memory() for r in host_rays]
+    d_in = [torch.empty_like(h, device=dev) for h in h_in]
+    n = [r.shape[0] for r in host_rays]
+    h_out = [torch.empty((n[0], 4), dtype=torch.int32).pin_memory(),
+             torch.empty((n[1], 4), dtype=torch.int32).pin_memory(),
+             torch.empty((n[2],), dtype=torch.int32).pin_memory()]
+    d_out = [torch.empty_like(h, device=dev) for h in h_out]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for h, d in zip(h_in, d_in):
+            d.copy_(h, non_blocking=True)
+        scion.scion_trace_closest(bvh, d_in[0], d_out[0])
+        scion.scion_trace_closest(bvh, d_in[1], d_out[1])
+        scion.scion_trace_any(bvh, d_in[2], d_out[2])
+        for h, d in zip(h_out, d_out):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush_l2(flush_buf)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    bi = sum(r.nbytes for r in host_rays)
+    bo = sum(h.numel() * 4 for h in h_out)
+    return times, bi, bo
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def cpu_oracle_workload(frac_den: int):
+    """A bounded sample of the workload traced by the CPU oracle's BVH2: every
+    frac_den-th primary ray, its bounce and shadow rays (generated from the
+    oracle's own primary hits). Returns (seconds, rays, threads)."""
+    import oracle
+    from paper_2511_15028_gb300 import scenes
+    sc = scenes.config2_scene()
+    tris = sc.triangles()
+    prim = scenes.config2_primary()[::frac_den].copy()
+    bvh = oracle.BVH2(tris, bins=32, leaf_max=4)
+    t0 = time.perf_counter()
+    h = bvh.closest(prim)
+    t1 = time.perf_counter()
+    bounce = scenes.bounce_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"], seed=2002)
+    shadow = scenes.shadow_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"])
+    t2 = time.perf_counter()
+    bvh.closest(bounce)
+    bvh.any(shadow)
+    t3 = time.perf_counter()
+    secs = (t1 - t0) + (t3 - t2)
+    return secs, prim.shape[0] + bounce.shape[0] + shadow.shape[0], oracle.max_threads()
+
+
+def cpu_baseline(target_s: float = 12.0):
+    secs, n, thr = cpu_oracle_workload(64)
+    den = max(1, min(64, int(64 * secs / target_s) or 1))
+    if den < 64:
+        secs, n, thr = cpu_oracle_workload(den)
+    return {"value": n / secs / 1e6, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
+            "sample": f"every {den}th primary ray of 1920x1080 ({n} rays incl. bounce+shadow), "
+                      f"oracle binned-SAH BVH2 traversal, build excluded, {secs:.2f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    den = 16
+    times, counts = [], []
+    for i in range(args.warmup + args.steps):
+        secs, n, thr = cpu_oracle_workload(den)
+        if i >= args.warmup:
+            times.append(secs)
+            counts.append(n)
+    ms = trimmed_mean([t * 1e3 for t in times])
+    val = float(np.mean(counts)) / (ms / 1e3) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mrays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f" (CPU sample: every {den}th primary ray)",
+                       "layout": "oracle BVH2 (32 bins, <=4 tris/leaf)"},
+            "cpu_baseline": {"value": val, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
+                             "sample": f"every {den}th primary ray + its bounce and shadow rays per step"},
+            "e2e": {"value": val, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=9)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--layouts", default="all", help="all | comma-separated sweep names")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2511_15028_gb300 import build as native_build
+    native_build.build()
+    from paper_2511_15028_gb300 import scion
+
+    layouts = scion.sweep_layouts()
+    if args.layouts != "all":
+        keep = args.layouts.split(",")
+        layouts = {k: v for k, v in layouts.items() if k in keep}
+    first = next(iter(layouts.values()))
+    sc, prim, bounce, shadow = make_workload(scion, torch, dev, first)
+    n_rays = (prim.shape[0], bounce.shape[0], shadow.shape[0])
+    rays = [torch.from_numpy(r).to(dev) for r in (prim, bounce, shadow)]
+    outs = [torch.empty((n_rays[0], 4), dtype=torch.int32, device=dev),
+            torch.empty((n_rays[1], 4), dtype=torch.int32, device=dev),
+            torch.empty((n_rays[2],), dtype=torch.int32, device=dev)]
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "of measured" if hbm_peak else "of fallback"
+    hbm_peak = hbm_peak or 6800.0
+
+    results = {}
+    for name, desc in layouts.items():
+        bvh = scion.scion_build(sc.verts, desc, sc.indices)
+        info = scion.scion_bvh_info(bvh)
+        # visit counters for algorithmic bytes (counting kernel, untimed)
+        _, cp = scion.scion_trace_stats(bvh, rays[0], 0)
+        _, cb = scion.scion_trace_stats(bvh, rays[1], 0)
+        _, cs = scion.scion_trace_stats(bvh, rays[2], 1)
+        cnt = [c.cpu().numpy() for c in (cp, cb, cs)]
+        sn, st = node_load_bytes(desc), tri_load_bytes(desc, True)
+        alg = [int(c[3]) * (32 + (16 if q < 2 else 4)) + int(c[0]) * sn + int(c[2]) * st
+               for q, c in enumerate(cnt)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        step, per, clocks = time_layout(scion, torch, bvh, rays, outs, args.steps, args.warmup, flush_buf,
+                                        ClockSampler(bus) if rank == 0 else None)
+        ms = trimmed_mean(step.tolist())
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        st_status = scion.scion_get_status(bvh)
+        per_ms = [trimmed_mean(per[:, i].tolist()) for i in range(3)]
+        results[name] = {
+            "mrays_s": world * sum(n_rays) / (ms / 1e3) / 1e6,
+            "ms_per_step": ms,
+            "per_query_ms": {"primary": per_ms[0], "bounce": per_ms[1], "shadow": per_ms[2]},
+            "per_query_mrays_s": {q: n_rays[i] / (per_ms[i] / 1e3) / 1e6
+                                  for i, q in enumerate(("primary", "bounce", "shadow"))},
+            "bvh_mb": (info["node_bytes"] + info["prim_bytes"]) / 1e6,
+            "node_mb": info["node_bytes"] / 1e6, "n_nodes": info["n_nodes"], "depth": info["depth"],
+            "bytes_per_ray": {q: alg[i] / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
+            "nodes_per_ray": {q: float(cnt[i][0]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
+            "tris_per_ray": {q: float(cnt[i][2]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
+            "alg_bytes": alg, "clocks": clocks, "device_status": st_status,
+        }
+        results[name]["_bvh"] = bvh
+
+    best = max(results, key=lambda k: results[k]["mrays_s"])
+    r = results[best]
+    # dominant kernel of the best layout's step
+    qi = int(np.argmax([r["per_query_ms"][q] for q in ("primary", "bounce", "shadow")]))
+    qn = ("primary", "bounce", "shadow")[qi]
+    dur_s = r["per_query_ms"][qn] / 1e3
+    achieved = r["alg_bytes"][qi] / dur_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": f"trace_kernel ({'closest' if qi < 2 else 'any'}, {best}, {qn} rays)",
+                "peak_source": peak_src}
+    # end to end through host buffers, best layout
+    e2e_t, bi, bo = e2e_layout(scion, torch, r["_bvh"], (prim, bounce, shadow), args.steps, args.warmup, flush_buf)
+    e2e_ms = trimmed_mean(e2e_t)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * sum(n_rays) / (e2e_ms / 1e3) / 1e6, "unit": "Mrays/s",
+           "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
+    for v in results.values():
+        v.pop("_bvh", None)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": r["mrays_s"], "unit": "Mrays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "layout": best, "rays_per_step": int(sum(n_rays)),
+                       "rays": {"primary": n_rays[0], "bounce": n_rays[1], "shadow": n_rays[2]},
+                       "l2": "flushed (512 MiB write) between timed steps",
+                       "timing": "CUDA events per launch; trimmed mean of K steps (drop 2/9 each side)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": r["clocks"], "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "bvh_mb": r["bvh_mb"],
+            "layouts": {k: {kk: vv for kk, vv in v.items() if kk not in ("alg_bytes",)} for k, v in results.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

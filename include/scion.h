@@ -158,6 +158,15 @@ scion_status scion_trace_any(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
                              uint32_t *d_occluded, const scion_trace_params *params,
                              scion_stream stream);
 
+/* Counting variant of the two traces, for measurement: the same results
+ * (query 0: closest hits into scion_hit[n]; query 1: any-hit flags into
+ * uint32[n]) plus visit counters added into d_counters (device uint64[4]):
+ * [0] interior nodes fetched, [1] leaves visited, [2] triangles tested,
+ * [3] rays traced. Slower than the plain calls; not for production use. */
+scion_status scion_trace_stats(scion_bvh bvh, const scion_ray *d_rays, uint64_t n, uint32_t query,
+                               void *d_out, const scion_trace_params *params, scion_stream stream,
+                               uint64_t *d_counters);
+
 /* Device status of the BVH since the last call: synchronises the stream,
  * returns SCION_OK or the first device-side error code, and clears it. */
 scion_status scion_get_status(scion_bvh bvh, scion_stream stream, scion_status *device_status);

@@ -78,20 +78,20 @@ scion_status upload(void **dst, const std::vector<T> &src, cudaStream_t s, uint6
   return SCION_OK;
 }
 
-TraceKernel pick_kernel(const scion_bvh b, int any) {
+TraceKernel pick_kernel(const scion_bvh b, int any, int stats) {
   const scion_layout_desc &d = b->desc;
   const int soa = (int)d.box_layout, cref = (int)d.child_ref;
-  if (b->own_box) return kernels_own(soa, cref, any);
+  if (b->own_box) return kernels_own(soa, cref, any, stats);
   switch (d.width * 10 + d.box_prec) {
-    case 20: return kernels_w2_p0(soa, cref, any);
-    case 21: return kernels_w2_p1(soa, cref, any);
-    case 22: return kernels_w2_p2(soa, cref, any);
-    case 40: return kernels_w4_p0(soa, cref, any);
-    case 41: return kernels_w4_p1(soa, cref, any);
-    case 42: return kernels_w4_p2(soa, cref, any);
-    case 80: return kernels_w8_p0(soa, cref, any);
-    case 81: return kernels_w8_p1(soa, cref, any);
-    case 82: return kernels_w8_p2(soa, cref, any);
+    case 20: return kernels_w2_p0(soa, cref, any, stats);
+    case 21: return kernels_w2_p1(soa, cref, any, stats);
+    case 22: return kernels_w2_p2(soa, cref, any, stats);
+    case 40: return kernels_w4_p0(soa, cref, any, stats);
+    case 41: return kernels_w4_p1(soa, cref, any, stats);
+    case 42: return kernels_w4_p2(soa, cref, any, stats);
+    case 80: return kernels_w8_p0(soa, cref, any, stats);
+    case 81: return kernels_w8_p1(soa, cref, any, stats);
+    case 82: return kernels_w8_p2(soa, cref, any, stats);
   }
   return nullptr;
 }
@@ -148,7 +148,8 @@ int device_sms(int dev) {
 }
 
 scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *out,
-                          const scion_trace_params *params, cudaStream_t stream, int any) {
+                          const scion_trace_params *params, cudaStream_t stream, int any,
+                          unsigned long long *stats = nullptr) {
   if (!b || (n > 0 && (!rays || !out))) return SCION_ERR_INVALID_ARG;
   if (n == 0) return SCION_OK;
   if ((reinterpret_cast<uintptr_t>(rays) & 15u) || (!any && (reinterpret_cast<uintptr_t>(out) & 15u)) ||
@@ -163,7 +164,7 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   if (smem_entries > 64) return SCION_ERR_INVALID_ARG;
   if (p.ordered_children > 2) return SCION_ERR_INVALID_ARG;
   const uint32_t ordered = p.ordered_children == 2 ? 0u : 1u;
-  TraceKernel k = pick_kernel(b, any);
+  TraceKernel k = pick_kernel(b, any, stats ? 1 : 0);
   if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
   const size_t smem = (size_t)tpb * smem_entries * sizeof(uint2);
   int dev = 0;
@@ -196,6 +197,7 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   a.work = reinterpret_cast<unsigned long long *>(b->d_scratch);
   a.exit_count = b->d_scratch + 2;
   a.status = b->d_scratch + 3;
+  a.stats = stats;
   void *args[] = {&a};
   SCION_CUDA(cudaLaunchKernel((const void *)k, dim3((unsigned)grid), dim3(tpb), args, smem, stream));
   return SCION_OK;
@@ -304,6 +306,14 @@ scion_status scion_trace_closest(scion_bvh b, const scion_ray *d_rays, uint64_t 
 scion_status scion_trace_any(scion_bvh b, const scion_ray *d_rays, uint64_t n, uint32_t *d_occluded,
                              const scion_trace_params *params, scion_stream stream) {
   return launch_trace(b, d_rays, n, d_occluded, params, reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+scion_status scion_trace_stats(scion_bvh b, const scion_ray *d_rays, uint64_t n, uint32_t query,
+                              void *d_out, const scion_trace_params *params, scion_stream stream,
+                              uint64_t *d_counters) {
+  if (!d_counters || query > 1 || (reinterpret_cast<uintptr_t>(d_counters) & 7u)) return SCION_ERR_INVALID_ARG;
+  return launch_trace(b, d_rays, n, d_out, params, reinterpret_cast<cudaStream_t>(stream), (int)query,
+                      reinterpret_cast<unsigned long long *>(d_counters));
 }
 
 scion_status scion_get_status(scion_bvh b, scion_stream stream, scion_status *device_status) {

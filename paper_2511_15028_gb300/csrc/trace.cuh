@@ -46,6 +46,12 @@ struct TraceArgs {
   unsigned long long *work; // persistent work counter (self-resetting)
   uint32_t *exit_count;     // CTAs finished (self-resetting)
   uint32_t *status;         // first device error code
+  unsigned long long *stats;  // counting kernels: nodes, leaves, prim tests, rays
+};
+
+// Per-thread visit counters of the counting (STATS) kernels.
+struct Counts {
+  uint32_t nodes = 0, leaves = 0, prims = 0;
 };
 
 constexpr int kLocalStack = 48;           // local-memory tail of the stack
@@ -209,10 +215,12 @@ struct Best {
 
 // Test the triangles [first, first + count). Closest: keep the lexicographic
 // minimum of (t, id). Any: return true at the first accepted hit.
-template <bool ANY>
+template <bool ANY, bool STATS>
 __device__ __forceinline__ bool visit_leaf(const TraceArgs &a, const Ray &r, uint32_t first,
-                                           uint32_t count, Best &b) {
+                                           uint32_t count, Best &b, Counts &cnt) {
+  if (STATS) cnt.leaves++;
   for (uint32_t i = first; i < first + count; ++i) {
+    if (STATS) cnt.prims++;
     float4 p0, p1, p2;
     uint32_t id;
     if (a.prim_indirect) {
@@ -271,9 +279,9 @@ struct WideNode {
   }
 };
 
-template <int W, int PREC, int SOA, int CREF, bool ANY>
+template <int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
 __device__ __forceinline__ bool trace_wide_ray(const TraceArgs &a, const Ray &r, Stack &st,
-                                               Best &b, uint32_t &err) {
+                                               Best &b, uint32_t &err, Counts &cnt) {
   using N = WideNode<W, PREC, SOA, CREF>;
   uint32_t cur = a.root_ref;
   uint32_t steps = 0;
@@ -281,6 +289,7 @@ __device__ __forceinline__ bool trace_wide_ray(const TraceArgs &a, const Ray &r,
   while (cur != kEmptyRef) {
     if (++steps > a.max_steps) { err = kErrIter; return false; }
     if (ref_is_interior(cur)) {
+      if (STATS) cnt.nodes++;
       const uint4 *np = a.nodes + (size_t)ref_node(cur) * (N::kStride / 16);
       uint4 q[N::NQ];
 #pragma unroll
@@ -359,7 +368,7 @@ __device__ __forceinline__ bool trace_wide_ray(const TraceArgs &a, const Ray &r,
       }
       if (next != kEmptyRef) { cur = next; continue; }
     } else {
-      if (visit_leaf<ANY>(a, r, ref_leaf_first(cur), ref_leaf_count(cur), b)) return true;
+      if (visit_leaf<ANY, STATS>(a, r, ref_leaf_first(cur), ref_leaf_count(cur), b, cnt)) return true;
     }
     // next stacked entry that can still hold a closer hit
     cur = kEmptyRef;
@@ -372,15 +381,16 @@ __device__ __forceinline__ bool trace_wide_ray(const TraceArgs &a, const Ray &r,
 }
 
 // ------------------------------------------------------------------ own-box node
-template <int SOA, int CREF, bool ANY>
+template <int SOA, int CREF, bool ANY, bool STATS>
 __device__ __forceinline__ bool trace_bin_ray(const TraceArgs &a, const Ray &r, Stack &st,
-                                              Best &b, uint32_t &err) {
+                                              Best &b, uint32_t &err, Counts &counts) {
   if (a.n_nodes == 0) return false;
   uint32_t cur = 0;
   uint32_t steps = 0;
   st.sp = 0;
   while (cur != kEmptyRef) {
     if (++steps > a.max_steps) { err = kErrIter; return false; }
+    if (STATS) counts.nodes++;
     float lo0, lo1, lo2, hi0, hi1, hi2;
     uint32_t ref, meta;
     if (SOA) {
@@ -402,7 +412,7 @@ __device__ __forceinline__ bool trace_bin_ray(const TraceArgs &a, const Ray &r, 
     if (slab(r, lo0, lo1, lo2, hi0, hi1, hi2, tlim, tn)) {
       const uint32_t cnt = bin_meta_count(meta);
       if (cnt > 0) {
-        if (visit_leaf<ANY>(a, r, ref, cnt, b)) return true;
+        if (visit_leaf<ANY, STATS>(a, r, ref, cnt, b, counts)) return true;
       } else {
         const uint32_t l = CREF == REF_DIRECT ? cur + 1 : ref;
         const uint32_t rr = CREF == REF_DIRECT ? cur + ref : ref + 1;
@@ -420,8 +430,10 @@ __device__ __forceinline__ bool trace_bin_ray(const TraceArgs &a, const Ray &r, 
 }
 
 // ------------------------------------------------------------------ kernel body
-template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY>
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
 __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
+  Counts cnt;
+  uint32_t n_rays = 0;
   extern __shared__ uint2 smem_stack[];
   Stack st;
   st.sh = smem_stack + threadIdx.x;
@@ -440,10 +452,11 @@ __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
       Best b{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_MISS};
       uint32_t err = 0;
       bool found = false;
+      if (STATS) n_rays++;
       if constexpr (OWN) {
-        found = trace_bin_ray<SOA, CREF, ANY>(a, r, st, b, err);
+        found = trace_bin_ray<SOA, CREF, ANY, STATS>(a, r, st, b, err, cnt);
       } else {
-        if (a.root_ref != kEmptyRef) found = trace_wide_ray<W, PREC, SOA, CREF, ANY>(a, r, st, b, err);
+        if (a.root_ref != kEmptyRef) found = trace_wide_ray<W, PREC, SOA, CREF, ANY, STATS>(a, r, st, b, err, cnt);
       }
       if (err) atomicCAS(a.status, 0u, err);
       if (ANY) {
@@ -454,6 +467,12 @@ __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
             make_uint4(__float_as_uint(b.t), __float_as_uint(b.u), __float_as_uint(b.v), b.id);
       }
     }
+  }
+  if (STATS) {
+    atomicAdd(a.stats + 0, (unsigned long long)cnt.nodes);
+    atomicAdd(a.stats + 1, (unsigned long long)cnt.leaves);
+    atomicAdd(a.stats + 2, (unsigned long long)cnt.prims);
+    atomicAdd(a.stats + 3, (unsigned long long)n_rays);
   }
   // the last CTA to finish resets the counters for the next launch
   __syncthreads();

@@ -18,18 +18,22 @@ namespace scion {
 #define SCION_GETTER SCION_CAT(SCION_CAT(SCION_CAT(kernels_w, SCION_W), _p), SCION_PREC)
 #endif
 
-template <int SOA, int CREF, bool ANY>
+template <int SOA, int CREF, bool ANY, bool STATS>
 __global__ void __launch_bounds__(kMaxThreadsPerBlock) trace_kernel(TraceArgs a) {
-  trace_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, ANY>(a);
+  trace_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, ANY, STATS>(a);
 }
 
-TraceKernel SCION_GETTER(int soa, int cref, int any) {
-  static const TraceKernel table[2][2][2] = {
-      {{trace_kernel<0, 0, false>, trace_kernel<0, 0, true>},
-       {trace_kernel<0, 1, false>, trace_kernel<0, 1, true>}},
-      {{trace_kernel<1, 0, false>, trace_kernel<1, 0, true>},
-       {trace_kernel<1, 1, false>, trace_kernel<1, 1, true>}}};
-  return table[soa & 1][cref & 1][any & 1];
+TraceKernel SCION_GETTER(int soa, int cref, int any, int stats) {
+  static const TraceKernel table[2][2][2][2] = {
+      {{{trace_kernel<0, 0, false, false>, trace_kernel<0, 0, false, true>},
+        {trace_kernel<0, 0, true, false>, trace_kernel<0, 0, true, true>}},
+       {{trace_kernel<0, 1, false, false>, trace_kernel<0, 1, false, true>},
+        {trace_kernel<0, 1, true, false>, trace_kernel<0, 1, true, true>}}},
+      {{{trace_kernel<1, 0, false, false>, trace_kernel<1, 0, false, true>},
+        {trace_kernel<1, 0, true, false>, trace_kernel<1, 0, true, true>}},
+       {{trace_kernel<1, 1, false, false>, trace_kernel<1, 1, false, true>},
+        {trace_kernel<1, 1, true, false>, trace_kernel<1, 1, true, true>}}}};
+  return table[soa & 1][cref & 1][any & 1][stats & 1];
 }
 
 }  // namespace scion

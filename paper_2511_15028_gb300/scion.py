@@ -101,6 +101,7 @@ def lib():
         L.scion_trace_closest.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
         L.scion_trace_any.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
         L.scion_get_status.argtypes = [P, P, P]
+        L.scion_trace_stats.argtypes = [P, P, U64, U32, P, ctypes.POINTER(TraceParams), P, P]
         L.scion_destroy.argtypes = [P]
         L.scion_destroy.restype = None
         L.scion_status_string.argtypes = [I]
@@ -116,6 +117,7 @@ def lib():
         L.scion_debug_f16_decode.argtypes = [U32]
         L.scion_debug_f16_decode.restype = ctypes.c_float
         for name in ("scion_build", "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
+                     "scion_trace_stats",
                      "scion_get_status", "scion_debug_build_host", "scion_debug_host_stats",
                      "scion_debug_host_decode"):
             getattr(L, name).restype = I
@@ -231,6 +233,21 @@ def scion_trace_any(bvh: BVH, rays, occluded=None, params=None, stream=None):
                                  ctypes.c_void_p(occluded.data_ptr()), _params(params),
                                  _stream_ptr(stream)), "scion_trace_any")
     return occluded
+
+
+def scion_trace_stats(bvh: BVH, rays, query: int = 0, params=None, stream=None):
+    """Counting trace: (results, counters) with counters = int64 tensor
+    [nodes fetched, leaves visited, triangles tested, rays]."""
+    import torch
+    assert rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous()
+    n = rays.shape[0]
+    out = (torch.empty((n, 4), dtype=torch.int32, device=rays.device) if query == 0
+           else torch.empty((n,), dtype=torch.int32, device=rays.device))
+    cnt = torch.zeros(4, dtype=torch.int64, device=rays.device)
+    _check(lib().scion_trace_stats(bvh.handle, ctypes.c_void_p(rays.data_ptr()), n, query,
+                                   ctypes.c_void_p(out.data_ptr()), _params(params), _stream_ptr(stream),
+                                   ctypes.c_void_p(cnt.data_ptr())), "scion_trace_stats")
+    return out, cnt
 
 
 def scion_get_status(bvh: BVH, stream=None) -> int:
