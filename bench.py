@@ -62,24 +62,31 @@ def tri_load_bytes(desc, indexed: bool) -> int:
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampled every 10 ms while the benchmark runs; only samples
+    taken inside the timed windows (host wall-clock) are kept."""
+    FIELDS = ("timestamp,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, bus_id: str | None):
+    def __init__(self, bus_id):
         self.bus_id = bus_id
         self.proc = None
+        self.windows = []
         self.path = os.path.join("/tmp", f"scion_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
         except OSError:
             self.proc = None
 
-    def stop(self) -> dict:
+    def window(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -87,6 +94,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        import datetime
         rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
@@ -94,21 +102,25 @@ class ClockSampler:
                 continue
             if self.bus_id and self.bus_id.lower()[-12:] not in f[1].lower():
                 continue
-            rows.append(f)
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            if any(a - 0.005 <= ts <= b + 0.005 for a, b in self.windows):
+                rows.append(f)
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        num = lambda x: float(x) if x.replace(".", "", 1).isdigit() else None  # noqa: E731
+        sm = [v for v in (num(r[2]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[3]) for r in rows) if v is not None]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             for nm, v in zip(names, r[6:10]):
                 if v.strip().lower() == "active":
                     reasons.add(nm)
-        loaded = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
-        return {"sm_mhz": float(np.median(loaded)) if loaded else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(rows)}
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
 
 
 # ------------------------------------------------------------------ workload
@@ -140,8 +152,7 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
         scion.scion_trace_any(bvh, d_s, o_s)
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
-    if sampler:
-        sampler.start()
+    t_start = time.time()
     for k in range(steps):
         flush_l2(flush_buf)
         e = ev[k]
@@ -153,10 +164,11 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
         scion.scion_trace_any(bvh, d_s, o_s)
         e[3].record(stream)
     torch.cuda.synchronize()
-    clocks = sampler.stop() if sampler else None
+    if sampler:
+        sampler.window(t_start, time.time())
     per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in ev])  # ms
     step = per.sum(axis=1)
-    return step, per, clocks
+    return step, per
 
 
 def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf):
@@ -199,60 +211,68 @@ def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf):
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
-def cpu_oracle_workload(frac_den: int):
-    """A bounded sample of the workload traced by the CPU oracle's BVH2: every
-    frac_den-th primary ray, its bounce and shadow rays (generated from the
-    oracle's own primary hits). Returns (seconds, rays, threads)."""
+def cpu_oracle_setup():
+    """The CPU oracle's own copy of the workload: its BVH2 over the scene, the
+    primary rays, and bounce / shadow rays generated from the oracle's own
+    primary hits (nothing here comes from the GPU path)."""
     import oracle
     from paper_2511_15028_gb300 import scenes
     sc = scenes.config2_scene()
-    tris = sc.triangles()
-    prim = scenes.config2_primary()[::frac_den].copy()
-    bvh = oracle.BVH2(tris, bins=32, leaf_max=4)
-    t0 = time.perf_counter()
+    prim = scenes.config2_primary()
+    bvh = oracle.BVH2(sc.triangles(), bins=32, leaf_max=4)
     h = bvh.closest(prim)
-    t1 = time.perf_counter()
     bounce = scenes.bounce_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"], seed=2002)
     shadow = scenes.shadow_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"])
-    t2 = time.perf_counter()
+    return bvh, prim, bounce, shadow
+
+
+def cpu_oracle_pass(bvh, prim, bounce, shadow):
+    """One pass of the workload on the host cores; returns (seconds, rays)."""
+    t0 = time.perf_counter()
+    bvh.closest(prim)
     bvh.closest(bounce)
     bvh.any(shadow)
-    t3 = time.perf_counter()
-    secs = (t1 - t0) + (t3 - t2)
-    return secs, prim.shape[0] + bounce.shape[0] + shadow.shape[0], oracle.max_threads()
+    return time.perf_counter() - t0, prim.shape[0] + bounce.shape[0] + shadow.shape[0]
 
 
 def cpu_baseline(target_s: float = 12.0):
-    secs, n, thr = cpu_oracle_workload(64)
-    den = max(1, min(64, int(64 * secs / target_s) or 1))
-    if den < 64:
-        secs, n, thr = cpu_oracle_workload(den)
-    return {"value": n / secs / 1e6, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
-            "sample": f"every {den}th primary ray of 1920x1080 ({n} rays incl. bounce+shadow), "
-                      f"oracle binned-SAH BVH2 traversal, build excluded, {secs:.2f} s"}
+    import oracle
+    bvh, prim, bounce, shadow = cpu_oracle_setup()
+    secs, n = cpu_oracle_pass(bvh, prim, bounce, shadow)
+    reps = max(1, min(200, int(math.ceil(target_s / max(secs, 1e-3)))))
+    tot_s, tot_n = 0.0, 0
+    for _ in range(reps):
+        s_, n_ = cpu_oracle_pass(bvh, prim, bounce, shadow)
+        tot_s += s_
+        tot_n += n_
+    return {"value": tot_n / tot_s / 1e6, "unit": "Mrays/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{reps} passes of the full step ({n} rays each: primary + bounce + shadow), "
+                      f"oracle binned-SAH BVH2 traversal (build excluded), {tot_s:.1f} s total"}
 
 
 def run_reference(args, rank):
+    """The oracle as it stands, on the host cores, on the same workload: each
+    step is one full pass (primary + bounce + shadow)."""
     if rank != 0:
         return
     import oracle
     oracle.build()
-    den = 16
+    bvh, prim, bounce, shadow = cpu_oracle_setup()
     times, counts = [], []
     for i in range(args.warmup + args.steps):
-        secs, n, thr = cpu_oracle_workload(den)
+        secs, n = cpu_oracle_pass(bvh, prim, bounce, shadow)
         if i >= args.warmup:
             times.append(secs)
             counts.append(n)
     ms = trimmed_mean([t * 1e3 for t in times])
     val = float(np.mean(counts)) / (ms / 1e3) / 1e6
+    thr = oracle.max_threads()
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mrays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD + f" (CPU sample: every {den}th primary ray)",
-                       "layout": "oracle BVH2 (32 bins, <=4 tris/leaf)"},
+            "config": {"workload": WORKLOAD, "layout": "oracle BVH2 (32 bins, <=4 tris/leaf)"},
             "cpu_baseline": {"value": val, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
-                             "sample": f"every {den}th primary ray + its bounce and shadow rays per step"},
+                             "sample": "one full pass of the step per timed step"},
             "e2e": {"value": val, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -314,6 +334,9 @@ def main():
     hbm_peak = hbm_peak or 6800.0
 
     results = {}
+    sampler = ClockSampler(bus) if rank == 0 else None
+    if sampler:
+        sampler.start()
     for name, desc in layouts.items():
         bvh = scion.scion_build(sc.verts, desc, sc.indices)
         info = scion.scion_bvh_info(bvh)
@@ -328,8 +351,7 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-        step, per, clocks = time_layout(scion, torch, bvh, rays, outs, args.steps, args.warmup, flush_buf,
-                                        ClockSampler(bus) if rank == 0 else None)
+        step, per = time_layout(scion, torch, bvh, rays, outs, args.steps, args.warmup, flush_buf, sampler)
         ms = trimmed_mean(step.tolist())
         if dist is not None:
             t = torch.tensor([ms], device=dev)
@@ -348,10 +370,11 @@ def main():
             "bytes_per_ray": {q: alg[i] / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
             "nodes_per_ray": {q: float(cnt[i][0]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
             "tris_per_ray": {q: float(cnt[i][2]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
-            "alg_bytes": alg, "clocks": clocks, "device_status": st_status,
+            "alg_bytes": alg, "device_status": st_status,
         }
         results[name]["_bvh"] = bvh
 
+    clocks = sampler.stop() if sampler else None
     best = max(results, key=lambda k: results[k]["mrays_s"])
     r = results[best]
     # dominant kernel of the best layout's step
@@ -390,7 +413,7 @@ def main():
                        "l2": "flushed (512 MiB write) between timed steps",
                        "timing": "CUDA events per launch; trimmed mean of K steps (drop 2/9 each side)",
                        "parallelism": f"replicas x{world}"},
-            "clocks": r["clocks"], "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * args.steps,
             "bvh_mb": r["bvh_mb"],
             "layouts": {k: {kk: vv for kk, vv in v.items() if kk not in ("alg_bytes",)} for k, v in results.items()},
