@@ -167,6 +167,31 @@ scion_status scion_trace_stats(scion_bvh bvh, const scion_ray *d_rays, uint64_t 
                                void *d_out, const scion_trace_params *params, scion_stream stream,
                                uint64_t *d_counters);
 
+/* Closest hit for callers that cannot allocate device memory when they
+ * trace — for example code running while a CUDA graph is captured in global
+ * capture mode, where cudaMalloc is not permitted, or an application that
+ * gives all device memory to its own arena and forbids later allocations.
+ * The paper has no counterpart; this is a property of this library only.
+ *
+ * Same arguments and results as scion_trace_closest (the BVH, rays and hits
+ * are the caller's, built and allocated beforehand). The traversal's work
+ * counters live in a fixed 256-byte device array that the library reserves
+ * on every GPU that loads it, for the life of the process; 16 bytes of it are
+ * used. The call allocates nothing and frees nothing: it clears those 16
+ * bytes with cudaMemsetAsync on `stream` and launches the kernel.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress), so make that first call before any stream
+ *    capture begins.
+ *  - Every call on a device shares the one array: calls that overlap on the
+ *    GPU (different streams, or concurrent graphs) race and give wrong
+ *    results. Order them on one stream.
+ *  - Device errors still set the BVH's status word (scion_get_status).
+ *  - n >= 2^62 is rejected with SCION_ERR_INVALID_ARG (the counter in the
+ *    array must not wrap); scion_last_error() names the limit. */
+scion_status scion_trace_closest_noalloc(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
+                                         scion_hit *d_hits, const scion_trace_params *params,
+                                         scion_stream stream);
+
 /* Device status of the BVH since the last call: synchronises the stream,
  * returns SCION_OK or the first device-side error code, and clears it. */
 scion_status scion_get_status(scion_bvh bvh, scion_stream stream, scion_status *device_status);

@@ -410,3 +410,108 @@ uint32_t scion_debug_f16_round(float x, int dir) {
 float scion_debug_f16_decode(uint32_t h) { return f16_to_f32((uint16_t)h); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free closest hit
+// Some callers must not allocate device memory while they trace: code that runs
+// while a CUDA graph is being captured in global capture mode (where
+// cudaMalloc is not permitted), or a host application that hands all device
+// memory to its own arena up front and forbids any later allocation.
+// scion_trace_closest_noalloc serves them: the traversal's per-launch work
+// counters live in the fixed array below, reserved once when the library's
+// device code is loaded, instead of in memory that scion_build allocated with
+// the BVH. The kernel itself is the same closest-hit kernel.
+namespace {
+constexpr size_t kStaticScratchBytes = 256;          // reserved per device until exit
+constexpr size_t kStaticScratchUsed = 16;            // u64 work counter + u32 exit counter
+constexpr uint64_t kStaticMaxRays = 1ull << 62;      // the 64-bit counter must not wrap
+static_assert(kStaticScratchUsed <= kStaticScratchBytes, "static scratch too small");
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up once
+// per device; in host code the symbol itself is only a host-side stand-in).
+scion_status static_scratch(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= kMaxDevices) {
+    g_last_error = "device ordinal out of range for the static scratch table";
+    return SCION_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return SCION_OK;
+}
+}  // namespace
+
+extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray *rays, uint64_t n,
+                                                    scion_hit *hits, const scion_trace_params *params,
+                                                    scion_stream stream) {
+  if (!b || (n > 0 && (!rays || !hits))) return SCION_ERR_INVALID_ARG;
+  if (n >= kStaticMaxRays) {
+    g_last_error = "scion_trace_closest_noalloc: n exceeds the static scratch counter range (2^62 rays)";
+    return SCION_ERR_INVALID_ARG;
+  }
+  if (n == 0) return SCION_OK;
+  if ((reinterpret_cast<uintptr_t>(rays) & 15u) || (reinterpret_cast<uintptr_t>(hits) & 15u))
+    return SCION_ERR_INVALID_ARG;
+  scion_trace_params p{};
+  if (params) p = *params;
+  if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch != 0 || p.ordered_children > 2)
+    return SCION_ERR_INVALID_ARG;
+  const uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
+  if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
+  const uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
+  if (smem_entries > 64) return SCION_ERR_INVALID_ARG;
+  TraceKernel k = pick_kernel(b, 0, 0);
+  if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  void *scratch = nullptr;
+  scion_status st = static_scratch(&scratch);
+  if (st != SCION_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the counters must start at zero; they keep the previous call's values
+  SCION_CUDA(cudaMemsetAsync(scratch, 0, kStaticScratchUsed, s));
+  const size_t smem = (size_t)tpb * smem_entries * sizeof(uint2);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint32_t ctas = p.ctas_per_sm;
+  if (ctas == 0) {
+    int nb = 0;
+    SCION_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k, (int)tpb, smem));
+    ctas = (uint32_t)std::max(nb, 1);
+  }
+  if (smem > 48 * 1024)
+    SCION_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
+  TraceArgs a;
+  a.nodes = static_cast<const uint4 *>(b->d_nodes);
+  a.nodes2 = static_cast<const uint2 *>(b->d_nodes2);
+  a.prims = static_cast<const float4 *>(b->d_prims);
+  a.prim_ids = static_cast<const uint32_t *>(b->d_prim_ids);
+  a.verts = static_cast<const float4 *>(b->d_verts);
+  a.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+  a.rays = reinterpret_cast<const float4 *>(rays);
+  a.out = hits;
+  a.n = n;
+  a.root_ref = b->root_ref;
+  a.n_nodes = b->n_nodes;
+  a.prim_indirect = b->desc.prim_ref;
+  a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
+  a.ordered = p.ordered_children == 2 ? 0u : 1u;
+  a.smem_stack = smem_entries;
+  a.work = static_cast<unsigned long long *>(scratch);
+  a.exit_count = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(scratch) + 8);
+  a.status = b->d_scratch + 3;  // device errors still go to the BVH's status word
+  a.stats = nullptr;
+  void *args[] = {&a};
+  SCION_CUDA(cudaLaunchKernel((const void *)k, dim3((unsigned)grid), dim3(tpb), args, smem, s));
+  return SCION_OK;
+}
