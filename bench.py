@@ -277,6 +277,121 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched (config 4)
+def bench_batched(scion, torch, steps, warmup, flush_buf, seed=1004):
+    """64 uneven scenes, each with its own rays and autotuned layout: one
+    graph-captured batched launch against 64 per-scene plain launches (same
+    layouts; and a fixed default layout). Hits must be identical."""
+    from paper_2511_15028_gb300 import autotune, scenes
+    t0 = time.time()
+    wl = scenes.config4_workload(seed=seed)
+    gen_s = time.time() - t0
+    tuner = autotune.Autotuner()
+    rays, chosen = [], []
+    t0 = time.time()
+    for i, (sc, r) in enumerate(wl):
+        d = torch.from_numpy(r).cuda()
+        rays.append(d)
+        chosen.append(tuner.tune(i, sc.verts, sc.indices, d))
+    tune_s = time.time() - t0
+    bvhs = [c.bvh for c in chosen]
+    params = [c.params for c in chosen]
+    batch = scion.Batch(bvhs, rays, params=params)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batch.launch(stream=stream)
+    plain_out = [torch.empty_like(h) for h in batch.hits]
+
+    def plain():
+        for b, r, o, p in zip(bvhs, rays, plain_out, params):
+            scion.scion_trace_closest(b, r, o, params=p or None)
+
+    default = scion.layout(width=4, box_layout="soa", prim_ref="direct")
+    dflt = [scion.scion_build(sc.verts, default, sc.indices) for sc, _ in wl]
+    dflt_out = [torch.empty_like(h) for h in batch.hits]
+
+    def plain_default():
+        for b, r, o in zip(dflt, rays, dflt_out):
+            scion.scion_trace_closest(b, r, o)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush_l2(flush_buf)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return trimmed_mean(ts)
+
+    t_batch = timed(g.replay)
+    t_plain = timed(plain)
+    t_dflt = timed(plain_default)
+    identical = all(torch.equal(a, b) for a, b in zip(batch.hits, plain_out))
+    n_rays = sum(r.shape[0] for r in rays)
+    n_tris = sum(sc.n_tris for sc, _ in wl)
+    picks = {}
+    for c in chosen:
+        k = c.name + ("/slot" if c.params else "/ordered")
+        picks[k] = picks.get(k, 0) + 1
+    return {"scenes": len(wl), "tris": int(n_tris), "rays": int(n_rays),
+            "batched_graph_ms": t_batch, "plain_same_layouts_ms": t_plain, "plain_default_layout_ms": t_dflt,
+            "mrays_s_batched": n_rays / (t_batch / 1e3) / 1e6,
+            "speedup_vs_plain": t_plain / t_batch, "speedup_vs_default": t_dflt / t_batch,
+            "hits_identical": bool(identical), "autotune_picks": picks,
+            "gen_s": round(gen_s, 1), "build_and_tune_s": round(tune_s, 1)}
+
+
+# ------------------------------------------------------------------ differentiation (config 5)
+def bench_backward(scion, torch, steps, warmup):
+    """Config-1 scene and rays, L = sum w t + a u + b v: forward alone against
+    forward + backward (dL/dvertex via FP32 atomics, dL/dray)."""
+    from paper_2511_15028_gb300 import scenes
+    sc = scenes.config1_scene()
+    rays = torch.from_numpy(scenes.config1_rays()).cuda()
+    w, a, b = scenes.config5_weights(rays.shape[0])
+    g = torch.from_numpy(np.stack([w, a, b], -1)).cuda()
+    bvh = scion.scion_build(sc.verts, scion.layout(width=4, box_layout="soa", prim_ref="direct"), sc.indices)
+    hits = torch.empty((rays.shape[0], 4), dtype=torch.int32, device="cuda")
+    gv = torch.zeros((sc.verts.shape[0], 3), dtype=torch.float32, device="cuda")
+    gr = torch.empty((rays.shape[0], 8), dtype=torch.float32, device="cuda")
+
+    def fwd():
+        scion.scion_trace_closest(bvh, rays, hits)
+
+    def fwd_bwd():
+        scion.scion_trace_closest(bvh, rays, hits)
+        gv.zero_()
+        scion.scion_trace_backward(bvh, rays, hits, g, grad_verts=gv, grad_rays=gr)
+
+    def timed(fn, reps=50):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            for _ in range(reps):
+                fn()
+            b_.record()
+            b_.synchronize()
+            ts.append(a_.elapsed_time(b_) / reps)
+        return trimmed_mean(ts)
+
+    tf, tfb = timed(fwd), timed(fwd_bwd)
+    n = rays.shape[0]
+    return {"rays": n, "fwd_ms": tf, "fwd_bwd_ms": tfb, "mrays_s_fwd": n / (tf / 1e3) / 1e6,
+            "mrays_s_fwd_bwd": n / (tfb / 1e3) / 1e6, "fwd_bwd_over_fwd": tfb / tf}
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -286,6 +401,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--layouts", default="all", help="all | comma-separated sweep names")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and backward measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -397,6 +513,10 @@ def main():
            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
     for v in results.values():
         v.pop("_bvh", None)
+    extra = {}
+    if not args.no_extra:
+        extra["batched"] = bench_batched(scion, torch, args.steps, args.warmup, flush_buf)
+        extra["backward"] = bench_backward(scion, torch, args.steps, args.warmup)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -417,6 +537,7 @@ def main():
             "gpu_launches": 3 * args.steps,
             "bvh_mb": r["bvh_mb"],
             "layouts": {k: {kk: vv for kk, vv in v.items() if kk not in ("alg_bytes",)} for k, v in results.items()},
+            **extra,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -112,7 +112,7 @@ typedef struct {
  *  smem_stack        : shared-memory stack entries per thread (default 16).
  *  ordered_children  : 0 or 1 = visit nearer children first (closest-hit),
  *                      2 = stored slot order.
- *  rays_per_fetch    : reserved (0).
+ *  rays_per_fetch    : reserved (0); each warp fetches 32 rays at a time.
  *  max_steps         : per-ray node+leaf visit limit (0 = derived from size).
  *  reserved          : must be 0. */
 typedef struct {
@@ -138,6 +138,15 @@ scion_status scion_build(const float *verts, uint64_t n_verts, const uint32_t *i
                          uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
                          scion_bvh *out);
 
+/* Several layouts of one scene from a single logical build (Section 5.1: the
+ * topology is fixed first, then packed into each physical layout). descs:
+ * n_desc descriptors that must agree on leaf_max and sah_bins (else
+ * INVALID_ARG); out: n_desc handles, all NULL on error. Other arguments and
+ * errors as scion_build. */
+scion_status scion_build_many(const float *verts, uint64_t n_verts, const uint32_t *indices,
+                              uint64_t n_tris, const scion_layout_desc *descs, uint32_t n_desc,
+                              scion_stream stream, scion_bvh *out);
+
 /* Sizes of the device buffers (bytes) and tree shape. Any output pointer may
  * be NULL. node_bytes: node buffer(s); prim_bytes: leaf primitive buffer
  * (direct triangles, or ids plus the index table for indirect); depth: levels
@@ -157,6 +166,24 @@ scion_status scion_trace_closest(scion_bvh bvh, const scion_ray *d_rays, uint64_
 scion_status scion_trace_any(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
                              uint32_t *d_occluded, const scion_trace_params *params,
                              scion_stream stream);
+
+/* Backward pass of scion_trace_closest (no counterpart in the paper, which
+ * has no gradient). Each hit ray's triangle is held fixed (the traversal's
+ * discrete choice); dL/d(t,u,v) is carried through the hit-point identity
+ * o + t d = (1-u-v) p0 + u p1 + v p2 to the triangle's three vertices and to
+ * the ray.
+ *  d_rays, d_hits : the forward call's rays and hits (device, n each).
+ *  d_grad_tuv     : device float[n][3], dL/dt, dL/du, dL/dv per ray.
+ *  d_grad_verts   : device float[n_verts][3] in the vertex order given to
+ *                   scion_build; contributions are ADDED (FP32 atomics, so the
+ *                   summation order, and the last bits, vary between runs).
+ *  d_grad_rays    : device scion_ray-shaped float[n][8] receiving dL/d(o, d)
+ *                   (tmin and tmax entries are 0), or NULL.
+ * Missed rays (prim = SCION_PRIM_MISS) and errored rays contribute nothing.
+ * The per-ray 3x3 solve is done in double precision. */
+scion_status scion_trace_backward(scion_bvh bvh, const scion_ray *d_rays, const scion_hit *d_hits,
+                                  const float *d_grad_tuv, uint64_t n, float *d_grad_verts,
+                                  scion_ray *d_grad_rays, scion_stream stream);
 
 /* Counting variant of the two traces, for measurement: the same results
  * (query 0: closest hits into scion_hit[n]; query 1: any-hit flags into
@@ -191,6 +218,41 @@ scion_status scion_trace_stats(scion_bvh bvh, const scion_ray *d_rays, uint64_t 
 scion_status scion_trace_closest_noalloc(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
                                          scion_hit *d_hits, const scion_trace_params *params,
                                          scion_stream stream);
+
+/* ---- Many scenes in one launch (closest hit). No counterpart in the paper,
+ * whose measurements (Section 9.2) show the best layout changes with the
+ * workload; this lets each scene keep the layout chosen for it while all of
+ * them run in one persistent launch.
+ *
+ * scion_batch_create records scene i = (bvhs[i], d_rays[i] (device
+ * scion_ray[n[i]]), d_hits[i] (device scion_hit[n[i]]), per_scene[i] or
+ * defaults) into a device table (it allocates and uploads; synchronous on
+ * `stream`). threads_per_block and smem_stack are taken from per_scene[0].
+ * Scenes whose layout is one of the batched node families (width-2 own-box
+ * AoS f32, width-4 SoA f32, width-8 SoA f16, width-8 AoS u8, each with direct
+ * child references; triangles direct or indirect) run in one persistent
+ * kernel; any other scene gets its own plain launch from scion_batch_launch.
+ * The pointers are captured: the buffers must stay valid until the batch is
+ * destroyed.
+ *
+ * scion_batch_launch issues the work on `stream`: no allocation, no host
+ * synchronisation, so it may be captured into a CUDA graph and replayed.
+ * Results are identical to scion_trace_closest on each scene. Launches of one
+ * batch must not overlap on the GPU (they share its counters). */
+typedef struct scion_batch_s *scion_batch;
+scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d_rays, const uint64_t *n,
+                                scion_hit *const *d_hits, uint32_t n_scenes,
+                                const scion_trace_params *per_scene, scion_stream stream,
+                                scion_batch *out);
+scion_status scion_batch_launch(scion_batch batch, scion_stream stream);
+/* Scenes in the single multi-scene launch / scenes traced by plain launches. */
+scion_status scion_batch_info(scion_batch batch, uint32_t *batched_scenes, uint32_t *plain_scenes);
+void scion_batch_destroy(scion_batch batch);
+
+/* One-shot form: create, launch, wait for the stream, destroy. */
+scion_status scion_trace_batched(const scion_bvh *bvhs, const scion_ray *const *d_rays, const uint64_t *n,
+                                 scion_hit *const *d_hits, uint32_t n_scenes,
+                                 const scion_trace_params *per_scene, scion_stream stream);
 
 /* Device status of the BVH since the last call: synchronises the stream,
  * returns SCION_OK or the first device-side error code, and clears it. */

@@ -87,7 +87,9 @@ static int tri_finite(const float *p) {
  *   det = (U + V) + W, miss if zero;
  *   T = fma(W, Sz*C[kz], fma(V, Sz*B[kz], U*(Sz*A[kz])));
  *   t = T/det, u = V/det (weight of p1), v = W/det (weight of p2);
- *   accept iff tmin <= t <= tmax. */
+ *   accept iff max(tmin, 0) <= t <= tmax: hits behind the origin are never
+ *   reported (the paper's slab test clamps the entry distance with max(0, .)
+ *   and its triangle test requires t > 0, App. G); a NaN tmin counts as 0. */
 static int tri_test(const float *o, const shear_t *s, float tmin, float tmax,
                     const float *p, float *t_out, float *u_out, float *v_out) {
   if (!tri_finite(p)) return 0;
@@ -130,7 +132,8 @@ static int tri_test(const float *o, const shear_t *s, float tmin, float tmax,
   const float UAz = U * Az;
   const float T = fmaf(W, Cz, fmaf(V, Bz, UAz));
   const float t = T / det;
-  if (!(t >= tmin && t <= tmax)) return 0;
+  const float tlo = tmin > 0.0f ? tmin : 0.0f;
+  if (!(t >= tlo && t <= tmax)) return 0;
   *t_out = t;
   *u_out = V / det;
   *v_out = W / det;
@@ -458,7 +461,8 @@ static void visit(trav_t *q, uint32_t id) {
   const onode *nd = &q->b->nodes[id];
   double tlim = q->ray[7];
   if (!q->any && q->best.t < tlim) tlim = q->best.t;
-  if (!box_overlap(nd, q->o, q->rd, q->ray + 4, q->ray[3], tlim)) return;
+  const double tlo = q->ray[3] > 0.0f ? q->ray[3] : 0.0;  /* as in tri_test */
+  if (!box_overlap(nd, q->o, q->rd, q->ray + 4, tlo, tlim)) return;
   if (nd->count > 0) {
     for (uint32_t i = nd->first; i < nd->first + nd->count; ++i) {
       uint32_t p = q->b->prim[i];

@@ -1,0 +1,83 @@
+"""Per-scene layout and traversal-parameter autotuner for the batched launch.
+
+The paper's design-space exploration (Section 9.2) finds that the best layout
+depends on the scene, the rays and the machine. Here that choice is made per
+scene by measurement: the scene is built once as a logical BVH2 and packed into
+every candidate layout (scion_build_many); a sample of the scene's own rays is
+traced with each (layout, parameters) candidate, timed with CUDA events; the
+fastest wins and the choice is cached under the caller's key.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+from . import scion
+
+# Node layouts the batched kernel runs in one launch (direct child references).
+CANDIDATE_LAYOUTS = {
+    "bvh2_aos_f32": dict(width=2, box_layout="aos", box_prec="f32"),
+    "bvh4_soa_f32": dict(width=4, box_layout="soa", box_prec="f32"),
+    "bvh8_soa_f16": dict(width=8, box_layout="soa", box_prec="f16"),
+    "bvh8_aos_u8": dict(width=8, box_layout="aos", box_prec="u8"),
+}
+CANDIDATE_PARAMS = {"ordered": {}, "slot_order": {"ordered_children": 2}}
+
+
+@dataclass
+class Choice:
+    name: str
+    desc: object
+    params: dict
+    bvh: object
+    times_ms: dict = field(default_factory=dict)
+
+
+class Autotuner:
+    def __init__(self, prim_refs=("direct",), params=None, sample: int = 8192, reps: int = 3):
+        self.descs = {}
+        for name, kw in CANDIDATE_LAYOUTS.items():
+            for pr in prim_refs:
+                self.descs[f"{name}_{pr}"] = scion.layout(prim_ref=pr, **kw)
+        self.params = params if params is not None else CANDIDATE_PARAMS
+        self.sample = sample
+        self.reps = reps
+        self.cache = {}
+
+    def _time(self, bvh, rays, params, out):
+        import torch
+        best = None
+        for _ in range(self.reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            scion.scion_trace_closest(bvh, rays, out, params=params or None)
+            b.record()
+            b.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        return best
+
+    def tune(self, key, verts, indices, rays) -> Choice:
+        """Pick (layout, params) for one scene; returns the chosen BVH."""
+        import torch
+        names = list(self.descs)
+        if key in self.cache:
+            name, pname = self.cache[key]
+            bvh = scion.scion_build(verts, self.descs[name], indices)
+            return Choice(name, self.descs[name], self.params[pname], bvh)
+        bvhs = scion.scion_build_many(verts, [self.descs[n] for n in names], indices)
+        n = rays.shape[0]
+        step = max(1, n // self.sample)
+        sample = rays[::step][: self.sample].contiguous()
+        out = torch.empty((sample.shape[0], 4), dtype=torch.int32, device=rays.device)
+        times = {}
+        for name, bvh in zip(names, bvhs):
+            for pname, p in self.params.items():
+                times[(name, pname)] = self._time(bvh, sample, p, out)
+        best = min(times, key=times.get)
+        self.cache[key] = best
+        chosen = bvhs[names.index(best[0])]
+        for b in bvhs:
+            if b is not chosen:
+                scion.scion_destroy(b)
+        return Choice(best[0], self.descs[best[0]], self.params[best[1]], chosen,
+                      {f"{a}/{b}": t for (a, b), t in times.items()})

@@ -11,6 +11,8 @@
 
 #include "../../include/scion.h"
 #include "../../include/scion_debug.h"
+#include "backward.h"
+#include "batched.h"
 #include "builder.h"
 #include "kernels.h"
 
@@ -96,6 +98,54 @@ TraceKernel pick_kernel(const scion_bvh b, int any, int stats) {
   return nullptr;
 }
 
+
+// Host half of scion_build_many: validate every descriptor (all must share
+// leaf_max and sah_bins), build the logical BVH2 once, pack each layout.
+scion_status build_host_many(const float *v, uint64_t n_verts, const uint32_t *ix, uint64_t n_tris,
+                             const scion_layout_desc *descs, uint32_t n_desc, std::vector<HostBVH> *hbs) {
+  if (!descs || n_desc == 0 || (n_tris > 0 && !v)) return SCION_ERR_INVALID_ARG;
+  if (n_tris >= kMaxPrims || n_verts >= (1ull << 32)) return SCION_ERR_INVALID_ARG;
+  if (!ix && n_verts != 3 * n_tris) return SCION_ERR_INVALID_ARG;
+  std::vector<scion_layout_desc> d(n_desc);
+  std::vector<bool> own(n_desc);
+  for (uint32_t i = 0; i < n_desc; ++i) {
+    bool ob = false;
+    scion_status st = normalize_desc(descs[i], &d[i], &ob);
+    if (st != SCION_OK) return st;
+    own[i] = ob;
+    if (d[i].leaf_max != d[0].leaf_max || d[i].sah_bins != d[0].sah_bins) {
+      g_last_error = "scion_build_many: descriptors differ in leaf_max or sah_bins";
+      return SCION_ERR_INVALID_ARG;
+    }
+  }
+  if (ix)
+    for (uint64_t i = 0; i < 3 * n_tris; ++i)
+      if (ix[i] >= n_verts) return SCION_ERR_INVALID_ARG;
+  BuildInput in{v, n_verts, ix, n_tris};
+  try {
+    const auto t0 = std::chrono::steady_clock::now();
+    LogicalBVH lb;
+    build_logical(in, d[0].sah_bins, d[0].leaf_max, &lb);
+    const double logical_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    hbs->resize(n_desc);
+    for (uint32_t i = 0; i < n_desc; ++i) {
+      const auto t1 = std::chrono::steady_clock::now();
+      std::string err;
+      scion_status st = pack_bvh(in, lb, d[i], own[i], &(*hbs)[i], &err);
+      if (st != SCION_OK) {
+        g_last_error = err;
+        return st;
+      }
+      (*hbs)[i].build_ms =
+          logical_ms + std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+    }
+  } catch (const std::bad_alloc &) {
+    g_last_error = "out of host memory";
+    return SCION_ERR_OOM;
+  }
+  return SCION_OK;
+}
 
 // Host half of scion_build: validate, build the logical BVH2, pack.
 scion_status build_host(const float *v, uint64_t n_verts, const uint32_t *ix, uint64_t n_tris,
@@ -203,60 +253,18 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   return SCION_OK;
 }
 
-}  // namespace
 
-extern "C" {
 
-const char *scion_status_string(scion_status s) {
-  switch (s) {
-    case SCION_OK: return "ok";
-    case SCION_ERR_INVALID_ARG: return "invalid argument";
-    case SCION_ERR_UNSUPPORTED_LAYOUT: return "unsupported layout";
-    case SCION_ERR_OOM: return "out of memory";
-    case SCION_ERR_CUDA: return "CUDA error";
-    case SCION_ERR_STACK_OVERFLOW: return "traversal stack overflow";
-    case SCION_ERR_ITER_LIMIT: return "traversal step limit";
-    case SCION_ERR_BAD_INPUT: return "bad input";
-  }
-  return "unknown status";
-}
-
-const char *scion_last_error(void) { return g_last_error.c_str(); }
-
-scion_status scion_build(const float *verts, uint64_t n_verts, const uint32_t *indices,
-                         uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
-                         scion_bvh *out) {
-  if (!out) return SCION_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (!desc || (n_tris > 0 && !verts)) return SCION_ERR_INVALID_ARG;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // host copies of device-resident inputs (a device-to-host boundary)
-  std::vector<float> hv;
-  std::vector<uint32_t> hi;
-  const float *v = verts;
-  const uint32_t *ix = indices;
-  if (verts && is_device_ptr(verts)) {
-    hv.resize(3 * n_verts);
-    SCION_CUDA(cudaMemcpyAsync(hv.data(), verts, hv.size() * 4, cudaMemcpyDeviceToHost, s));
-    SCION_CUDA(cudaStreamSynchronize(s));
-    v = hv.data();
-  }
-  if (indices && is_device_ptr(indices)) {
-    hi.resize(3 * n_tris);
-    SCION_CUDA(cudaMemcpyAsync(hi.data(), indices, hi.size() * 4, cudaMemcpyDeviceToHost, s));
-    SCION_CUDA(cudaStreamSynchronize(s));
-    ix = hi.data();
-  }
-  HostBVH hb;
-  scion_status st = build_host(v, n_verts, ix, n_tris, desc, &hb);
-  if (st != SCION_OK) return st;
+// Upload one packed BVH; on failure everything is freed and *out stays null.
+scion_status upload_bvh(HostBVH &hb, uint64_t n_tris, uint64_t n_verts, bool indexed, cudaStream_t s,
+                        scion_bvh *out) {
   scion_bvh b = new (std::nothrow) scion_bvh_s();
   if (!b) return SCION_ERR_OOM;
   b->desc = hb.desc;
   b->own_box = hb.own_box;
   b->n_tris = (uint32_t)n_tris;
   b->n_verts = (uint32_t)n_verts;
-  b->indexed = ix != nullptr;
+  b->indexed = indexed;
   b->n_nodes = hb.n_nodes;
   b->node_stride = hb.node_stride;
   b->n_leaf_entries = hb.n_leaf_entries;
@@ -288,6 +296,96 @@ scion_status scion_build(const float *verts, uint64_t n_verts, const uint32_t *i
   return SCION_OK;
 }
 
+// Host copies of device-resident inputs (a device-to-host boundary).
+scion_status host_inputs(const float *verts, uint64_t n_verts, const uint32_t *indices, uint64_t n_tris,
+                         cudaStream_t s, std::vector<float> *hv, std::vector<uint32_t> *hi,
+                         const float **v, const uint32_t **ix) {
+  *v = verts;
+  *ix = indices;
+  if (verts && is_device_ptr(verts)) {
+    hv->resize(3 * n_verts);
+    SCION_CUDA(cudaMemcpyAsync(hv->data(), verts, hv->size() * 4, cudaMemcpyDeviceToHost, s));
+    SCION_CUDA(cudaStreamSynchronize(s));
+    *v = hv->data();
+  }
+  if (indices && is_device_ptr(indices)) {
+    hi->resize(3 * n_tris);
+    SCION_CUDA(cudaMemcpyAsync(hi->data(), indices, hi->size() * 4, cudaMemcpyDeviceToHost, s));
+    SCION_CUDA(cudaStreamSynchronize(s));
+    *ix = hi->data();
+  }
+  return SCION_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *scion_status_string(scion_status s) {
+  switch (s) {
+    case SCION_OK: return "ok";
+    case SCION_ERR_INVALID_ARG: return "invalid argument";
+    case SCION_ERR_UNSUPPORTED_LAYOUT: return "unsupported layout";
+    case SCION_ERR_OOM: return "out of memory";
+    case SCION_ERR_CUDA: return "CUDA error";
+    case SCION_ERR_STACK_OVERFLOW: return "traversal stack overflow";
+    case SCION_ERR_ITER_LIMIT: return "traversal step limit";
+    case SCION_ERR_BAD_INPUT: return "bad input";
+  }
+  return "unknown status";
+}
+
+const char *scion_last_error(void) { return g_last_error.c_str(); }
+
+scion_status scion_build(const float *verts, uint64_t n_verts, const uint32_t *indices,
+                         uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
+                         scion_bvh *out) {
+  if (!out) return SCION_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc || (n_tris > 0 && !verts)) return SCION_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<float> hv;
+  std::vector<uint32_t> hi;
+  const float *v;
+  const uint32_t *ix;
+  scion_status st = host_inputs(verts, n_verts, indices, n_tris, s, &hv, &hi, &v, &ix);
+  if (st != SCION_OK) return st;
+  HostBVH hb;
+  st = build_host(v, n_verts, ix, n_tris, desc, &hb);
+  if (st != SCION_OK) return st;
+  return upload_bvh(hb, n_tris, n_verts, ix != nullptr, s, out);
+}
+
+scion_status scion_build_many(const float *verts, uint64_t n_verts, const uint32_t *indices,
+                              uint64_t n_tris, const scion_layout_desc *descs, uint32_t n_desc,
+                              scion_stream stream, scion_bvh *out) {
+  if (!out || !descs || n_desc == 0) return SCION_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < n_desc; ++i) out[i] = nullptr;
+  if (n_tris > 0 && !verts) return SCION_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<float> hv;
+  std::vector<uint32_t> hi;
+  const float *v;
+  const uint32_t *ix;
+  scion_status st = host_inputs(verts, n_verts, indices, n_tris, s, &hv, &hi, &v, &ix);
+  if (st != SCION_OK) return st;
+  std::vector<HostBVH> hbs;
+  st = build_host_many(v, n_verts, ix, n_tris, descs, n_desc, &hbs);
+  if (st != SCION_OK) return st;
+  for (uint32_t i = 0; i < n_desc; ++i) {
+    st = upload_bvh(hbs[i], n_tris, n_verts, ix != nullptr, s, &out[i]);
+    if (st != SCION_OK) {
+      for (uint32_t j = 0; j < i; ++j) {
+        free_bvh(out[j]);
+        out[j] = nullptr;
+      }
+      return st;
+    }
+    hbs[i] = HostBVH();  // release host memory early
+  }
+  return SCION_OK;
+}
+
 scion_status scion_bvh_info(scion_bvh b, uint64_t *node_bytes, uint64_t *prim_bytes, uint32_t *depth,
                             uint32_t *n_nodes) {
   if (!b) return SCION_ERR_INVALID_ARG;
@@ -314,6 +412,181 @@ scion_status scion_trace_stats(scion_bvh b, const scion_ray *d_rays, uint64_t n,
   if (!d_counters || query > 1 || (reinterpret_cast<uintptr_t>(d_counters) & 7u)) return SCION_ERR_INVALID_ARG;
   return launch_trace(b, d_rays, n, d_out, params, reinterpret_cast<cudaStream_t>(stream), (int)query,
                       reinterpret_cast<unsigned long long *>(d_counters));
+}
+
+scion_status scion_trace_backward(scion_bvh b, const scion_ray *d_rays, const scion_hit *d_hits,
+                                  const float *d_grad_tuv, uint64_t n, float *d_grad_verts,
+                                  scion_ray *d_grad_rays, scion_stream stream) {
+  if (!b || (n > 0 && (!d_rays || !d_hits || !d_grad_tuv || !d_grad_verts))) return SCION_ERR_INVALID_ARG;
+  if (n == 0) return SCION_OK;
+  if ((reinterpret_cast<uintptr_t>(d_rays) & 15u) || (reinterpret_cast<uintptr_t>(d_hits) & 15u) ||
+      (reinterpret_cast<uintptr_t>(d_grad_rays) & 15u) || (reinterpret_cast<uintptr_t>(d_grad_tuv) & 3u) ||
+      (reinterpret_cast<uintptr_t>(d_grad_verts) & 3u))
+    return SCION_ERR_INVALID_ARG;
+  BackwardArgs a;
+  a.rays = reinterpret_cast<const float *>(d_rays);
+  a.hits = reinterpret_cast<const uint32_t *>(d_hits);
+  a.grad_tuv = d_grad_tuv;
+  a.verts = static_cast<const float4 *>(b->d_verts);
+  a.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+  a.grad_verts = d_grad_verts;
+  a.grad_rays = reinterpret_cast<float *>(d_grad_rays);
+  a.n = n;
+  a.n_tris = b->n_tris;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  SCION_CUDA(launch_backward(a, device_sms(dev), reinterpret_cast<cudaStream_t>(stream)));
+  return SCION_OK;
+}
+
+// ---------------------------------------------------------------- batched
+struct scion_batch_s {
+  BatchScene *d_scenes = nullptr;   // scene table (device)
+  uint32_t *d_counters = nullptr;   // u64 work counter + u32 exit counter
+  uint32_t n_scenes = 0;            // scenes in the multi-family launch
+  unsigned long long total = 0;     // padded global ray count
+  uint32_t threads = 256, smem_stack = 16, grid = 0;
+  // scenes whose layout the batched kernel does not handle: plain launches
+  std::vector<scion_bvh> rest_bvh;
+  std::vector<const scion_ray *> rest_rays;
+  std::vector<uint64_t> rest_n;
+  std::vector<scion_hit *> rest_hits;
+  std::vector<scion_trace_params> rest_params;
+};
+
+scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d_rays, const uint64_t *n,
+                                scion_hit *const *d_hits, uint32_t n_scenes,
+                                const scion_trace_params *per_scene, scion_stream stream, scion_batch *out) {
+  if (!out) return SCION_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n_scenes > 0 && (!bvhs || !d_rays || !n || !d_hits)) return SCION_ERR_INVALID_ARG;
+  scion_batch bt = new (std::nothrow) scion_batch_s();
+  if (!bt) return SCION_ERR_OOM;
+  std::vector<BatchScene> table;
+  unsigned long long total = 0;
+  if (per_scene) {
+    bt->threads = per_scene[0].threads_per_block ? per_scene[0].threads_per_block : 256;
+    bt->smem_stack = per_scene[0].smem_stack ? per_scene[0].smem_stack : 16;
+  }
+  if (bt->threads % 32 || bt->threads > (uint32_t)kMaxThreadsPerBlock || bt->smem_stack > 64) {
+    delete bt;
+    return SCION_ERR_INVALID_ARG;
+  }
+  for (uint32_t i = 0; i < n_scenes; ++i) {
+    scion_bvh b = bvhs[i];
+    scion_trace_params p{};
+    if (per_scene) p = per_scene[i];
+    if (!b || (n[i] > 0 && (!d_rays[i] || !d_hits[i])) || p.ordered_children > 2 ||
+        (reinterpret_cast<uintptr_t>(d_rays[i]) & 15u) || (reinterpret_cast<uintptr_t>(d_hits[i]) & 15u)) {
+      delete bt;
+      return SCION_ERR_INVALID_ARG;
+    }
+    if (n[i] == 0) continue;
+    const int fam = batched_family(b->own_box ? 1u : 0u, b->desc);
+    if (fam < 0) {
+      bt->rest_bvh.push_back(b);
+      bt->rest_rays.push_back(d_rays[i]);
+      bt->rest_n.push_back(n[i]);
+      bt->rest_hits.push_back(d_hits[i]);
+      bt->rest_params.push_back(p);
+      continue;
+    }
+    BatchScene sc{};
+    TraceArgs &a = sc.a;
+    a.nodes = static_cast<const uint4 *>(b->d_nodes);
+    a.nodes2 = static_cast<const uint2 *>(b->d_nodes2);
+    a.prims = static_cast<const float4 *>(b->d_prims);
+    a.prim_ids = static_cast<const uint32_t *>(b->d_prim_ids);
+    a.verts = static_cast<const float4 *>(b->d_verts);
+    a.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+    a.rays = reinterpret_cast<const float4 *>(d_rays[i]);
+    a.out = d_hits[i];
+    a.n = n[i];
+    a.root_ref = b->root_ref;
+    a.n_nodes = b->n_nodes;
+    a.prim_indirect = b->desc.prim_ref;
+    a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
+    a.ordered = p.ordered_children == 2 ? 0u : 1u;
+    a.smem_stack = bt->smem_stack;
+    a.status = b->d_scratch + 3;
+    sc.begin = total;
+    sc.family = (uint32_t)fam;
+    total += (n[i] + 31) / 32 * 32;
+    table.push_back(sc);
+  }
+  bt->n_scenes = (uint32_t)table.size();
+  bt->total = total;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&bt->d_counters), 16);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->d_counters, 0, 16, s);
+  if (e == cudaSuccess && !table.empty()) {
+    e = cudaMalloc(reinterpret_cast<void **>(&bt->d_scenes), table.size() * sizeof(BatchScene));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bt->d_scenes, table.data(), table.size() * sizeof(BatchScene), cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && !table.empty()) {
+    const size_t smem = (size_t)bt->threads * bt->smem_stack * sizeof(uint2);
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel_ptr(), (int)bt->threads, smem);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t want = ((uint64_t)total + bt->threads - 1) / bt->threads;
+    bt->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)std::max(nb, 1) * device_sms(dev), want));
+  }
+  if (e != cudaSuccess) {
+    if (bt->d_counters) cudaFree(bt->d_counters);
+    if (bt->d_scenes) cudaFree(bt->d_scenes);
+    delete bt;
+    if (e == cudaErrorMemoryAllocation) return SCION_ERR_OOM;
+    return cuda_fail(e);
+  }
+  *out = bt;
+  return SCION_OK;
+}
+
+scion_status scion_batch_launch(scion_batch bt, scion_stream stream) {
+  if (!bt) return SCION_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (bt->n_scenes > 0)
+    SCION_CUDA(launch_batched(bt->d_scenes, bt->n_scenes, bt->total,
+                              reinterpret_cast<unsigned long long *>(bt->d_counters), bt->d_counters + 2,
+                              bt->smem_stack, bt->threads, bt->grid, s));
+  for (size_t i = 0; i < bt->rest_bvh.size(); ++i) {
+    scion_status st = launch_trace(bt->rest_bvh[i], bt->rest_rays[i], bt->rest_n[i], bt->rest_hits[i],
+                                   &bt->rest_params[i], s, 0);
+    if (st != SCION_OK) return st;
+  }
+  return SCION_OK;
+}
+
+void scion_batch_destroy(scion_batch bt) {
+  if (!bt) return;
+  if (bt->d_counters) cudaFree(bt->d_counters);
+  if (bt->d_scenes) cudaFree(bt->d_scenes);
+  delete bt;
+}
+
+scion_status scion_batch_info(scion_batch bt, uint32_t *batched_scenes, uint32_t *plain_scenes) {
+  if (!bt) return SCION_ERR_INVALID_ARG;
+  if (batched_scenes) *batched_scenes = bt->n_scenes;
+  if (plain_scenes) *plain_scenes = (uint32_t)bt->rest_bvh.size();
+  return SCION_OK;
+}
+
+scion_status scion_trace_batched(const scion_bvh *bvhs, const scion_ray *const *d_rays, const uint64_t *n,
+                                 scion_hit *const *d_hits, uint32_t n_scenes,
+                                 const scion_trace_params *per_scene, scion_stream stream) {
+  scion_batch bt = nullptr;
+  scion_status st = scion_batch_create(bvhs, d_rays, n, d_hits, n_scenes, per_scene, stream, &bt);
+  if (st != SCION_OK) return st;
+  st = scion_batch_launch(bt, stream);
+  // the table must outlive the launch: wait for it before releasing
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  scion_batch_destroy(bt);
+  if (st != SCION_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e);
+  return SCION_OK;
 }
 
 scion_status scion_get_status(scion_bvh b, scion_stream stream, scion_status *device_status) {

@@ -86,8 +86,11 @@ scion_status normalize_desc(const scion_layout_desc &in, scion_layout_desc *out,
 // ------------------------------------------------------------ SAH BVH2
 namespace {
 
+// Per-triangle record moved by the partitions, so every pass over a node's
+// range reads memory sequentially.
 struct PrimInfo {
   float lo[3], hi[3], c[3];
+  uint32_t id;
 };
 
 inline void box_empty(Box3 &b) {
@@ -121,17 +124,21 @@ struct Bins {
 
 class SahBuilder {
  public:
-  SahBuilder(const std::vector<PrimInfo> &info, uint32_t bins, uint32_t leaf_max, LogicalBVH *out)
-      : info_(info), bins_((int)bins), leaf_max_(leaf_max), out_(out) {}
+  SahBuilder(std::vector<PrimInfo> &recs, uint32_t bins, uint32_t leaf_max, LogicalBVH *out)
+      : recs_(recs), bins_((int)bins), leaf_max_(leaf_max), out_(out) {}
 
   void run() {
-    const uint32_t n = (uint32_t)out_->prims.size();
+    const uint32_t n = (uint32_t)recs_.size();
     out_->nodes.assign(n ? 2 * (size_t)n - 1 : 0, LNode{});
     next_ = 0;
-    if (n == 0) return;
+    if (n == 0) {
+      out_->prims.clear();
+      return;
+    }
+    tmp_.resize(n);
     struct Task { uint32_t id, first, count; };
     std::vector<Task> big{{alloc(), 0, n}}, small;
-    const uint32_t kSerial = 1u << 16;
+    const uint32_t kSerial = 1u << 15;
     while (!big.empty()) {
       Task t = big.back();
       big.pop_back();
@@ -141,45 +148,60 @@ class SahBuilder {
       (lt.count > kSerial ? big : small).push_back(lt);
       (rt.count > kSerial ? big : small).push_back(rt);
     }
+    std::sort(small.begin(), small.end(), [](const Task &a, const Task &b) { return a.count > b.count; });
     const long ns = (long)small.size();
 #pragma omp parallel for schedule(dynamic, 1)
     for (long i = 0; i < ns; ++i) build_serial(small[i].id, small[i].first, small[i].count);
     out_->nodes.resize(next_.load());
+    out_->prims.resize(n);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < (long)n; ++i) out_->prims[i] = recs_[i].id;
   }
 
  private:
   uint32_t alloc() { return next_.fetch_add(1); }
 
+  static int threads() {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+  }
+  static int thread_id() {
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+  }
+
   void bounds(uint32_t first, uint32_t count, bool par, Box3 *nb, Box3 *cb) {
     box_empty(*nb);
     box_empty(*cb);
-    const uint32_t *p = out_->prims.data();
+    const PrimInfo *q = recs_.data();
     if (par && count > 4096) {
-#ifdef _OPENMP
-      const int nt = omp_get_max_threads();
-#else
-      const int nt = 1;
-#endif
-      std::vector<Box3> nbs(nt), cbs(nt);
-      for (int i = 0; i < nt; ++i) { box_empty(nbs[i]); box_empty(cbs[i]); }
-#pragma omp parallel for schedule(static)
-      for (long i = first; i < (long)(first + count); ++i) {
-#ifdef _OPENMP
-        const int tid = omp_get_thread_num();
-#else
-        const int tid = 0;
-#endif
-        const PrimInfo &q = info_[p[i]];
-        box_grow(nbs[tid], q.lo, q.hi);
-        box_grow(cbs[tid], q.c, q.c);
+#pragma omp parallel
+      {
+        Box3 ln, lc;  // thread-local: no shared cache lines in the loop
+        box_empty(ln);
+        box_empty(lc);
+#pragma omp for schedule(static) nowait
+        for (long i = first; i < (long)(first + count); ++i) {
+          box_grow(ln, q[i].lo, q[i].hi);
+          box_grow(lc, q[i].c, q[i].c);
+        }
+#pragma omp critical(scion_bounds_merge)
+        {
+          box_merge(*nb, ln);
+          box_merge(*cb, lc);
+        }
       }
-      for (int i = 0; i < nt; ++i) { box_merge(*nb, nbs[i]); box_merge(*cb, cbs[i]); }
       return;
     }
     for (uint32_t i = first; i < first + count; ++i) {
-      const PrimInfo &q = info_[p[i]];
-      box_grow(*nb, q.lo, q.hi);
-      box_grow(*cb, q.c, q.c);
+      box_grow(*nb, q[i].lo, q[i].hi);
+      box_grow(*cb, q[i].c, q[i].c);
     }
   }
 
@@ -190,47 +212,74 @@ class SahBuilder {
 
   void bin(uint32_t first, uint32_t count, const Box3 &cb, const float *scale, bool par, Bins *bn) {
     bn->clear(bins_);
-    const uint32_t *p = out_->prims.data();
+    const PrimInfo *q = recs_.data();
     if (par && count > 4096) {
-#ifdef _OPENMP
-      const int nt = omp_get_max_threads();
-#else
-      const int nt = 1;
-#endif
-      std::vector<Bins> loc(nt);
-      for (auto &b : loc) b.clear(bins_);
-#pragma omp parallel for schedule(static)
-      for (long i = first; i < (long)(first + count); ++i) {
-#ifdef _OPENMP
-        Bins &b = loc[omp_get_thread_num()];
-#else
-        Bins &b = loc[0];
-#endif
-        const PrimInfo &q = info_[p[i]];
-        for (int a = 0; a < 3; ++a) {
-          if (!(scale[a] > 0.f)) continue;
-          int k = bin_of(q, a, cb, scale[a]);
-          b.cnt[a][k]++;
-          box_grow(b.box[a][k], q.lo, q.hi);
+#pragma omp parallel
+      {
+        Bins b;  // thread-local
+        b.clear(bins_);
+#pragma omp for schedule(static) nowait
+        for (long i = first; i < (long)(first + count); ++i) {
+          for (int a = 0; a < 3; ++a) {
+            if (!(scale[a] > 0.f)) continue;
+            int k = bin_of(q[i], a, cb, scale[a]);
+            b.cnt[a][k]++;
+            box_grow(b.box[a][k], q[i].lo, q[i].hi);
+          }
         }
-      }
-      for (auto &b : loc)
+#pragma omp critical(scion_bins_merge)
         for (int a = 0; a < 3; ++a)
           for (int k = 0; k < bins_; ++k) {
             bn->cnt[a][k] += b.cnt[a][k];
             box_merge(bn->box[a][k], b.box[a][k]);
           }
+      }
       return;
     }
     for (uint32_t i = first; i < first + count; ++i) {
-      const PrimInfo &q = info_[p[i]];
       for (int a = 0; a < 3; ++a) {
         if (!(scale[a] > 0.f)) continue;
-        int k = bin_of(q, a, cb, scale[a]);
+        int k = bin_of(q[i], a, cb, scale[a]);
         bn->cnt[a][k]++;
-        box_grow(bn->box[a][k], q.lo, q.hi);
+        box_grow(bn->box[a][k], q[i].lo, q[i].hi);
       }
     }
+  }
+
+  // Stable two-way partition of a large range through the scratch buffer:
+  // per-chunk counts, prefix sums, parallel scatter, parallel copy back.
+  uint32_t par_partition(uint32_t first, uint32_t count, int axis, int split, const Box3 &cb, float scale) {
+    const int nt = threads();
+    const uint32_t nch = (uint32_t)nt * 4;
+    const uint32_t per = (count + nch - 1) / nch;
+    std::vector<uint32_t> nl(nch, 0), nr(nch, 0);
+    PrimInfo *q = recs_.data();
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < (long)nch; ++c) {
+      const uint32_t b = first + (uint32_t)c * per, e = std::min(first + count, b + per);
+      uint32_t l = 0;
+      for (uint32_t i = b; i < e; ++i) l += bin_of(q[i], axis, cb, scale) <= split;
+      nl[c] = l;
+      nr[c] = e > b ? (e - b) - l : 0;
+    }
+    std::vector<uint32_t> ol(nch), orr(nch);
+    uint32_t accl = 0;
+    for (uint32_t c = 0; c < nch; ++c) { ol[c] = accl; accl += nl[c]; }
+    uint32_t accr = accl;
+    for (uint32_t c = 0; c < nch; ++c) { orr[c] = accr; accr += nr[c]; }
+    PrimInfo *t = tmp_.data();
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < (long)nch; ++c) {
+      const uint32_t b = first + (uint32_t)c * per, e = std::min(first + count, b + per);
+      uint32_t pl = first + ol[c], pr = first + orr[c];
+      for (uint32_t i = b; i < e; ++i) {
+        if (bin_of(q[i], axis, cb, scale) <= split) t[pl++] = q[i];
+        else t[pr++] = q[i];
+      }
+    }
+#pragma omp parallel for schedule(static)
+    for (long i = first; i < (long)(first + count); ++i) q[i] = t[i];
+    return first + accl;
   }
 
   // Decide leaf or split for node `id`; on a split allocate the children and
@@ -285,7 +334,7 @@ class SahBuilder {
       nd.axis = 0;
       return false;
     }
-    uint32_t *p = out_->prims.data();
+    PrimInfo *q = recs_.data();
     uint32_t mid;
     int axis = best_axis;
     if (best_axis < 0) {
@@ -294,10 +343,15 @@ class SahBuilder {
       for (int a = 0; a < 3; ++a)
         if (nb.hi[a] - nb.lo[a] > ext) { ext = nb.hi[a] - nb.lo[a]; axis = a; }
     } else {
-      uint32_t *m = std::partition(p + first, p + first + count, [&](uint32_t q) {
-        return bin_of(info_[q], best_axis, cb, scale[best_axis]) <= best_bin;
-      });
-      mid = (uint32_t)(m - p);
+      const float sc = scale[best_axis];
+      if (par && count > (1u << 18)) {
+        mid = par_partition(first, count, best_axis, best_bin, cb, sc);
+      } else {
+        PrimInfo *m = std::partition(q + first, q + first + count, [&](const PrimInfo &x) {
+          return bin_of(x, best_axis, cb, sc) <= best_bin;
+        });
+        mid = (uint32_t)(m - q);
+      }
       if (mid == first || mid == first + count) mid = first + count / 2;
     }
     nd.count = 0;
@@ -318,7 +372,8 @@ class SahBuilder {
     build_serial(r, mid, first + count - mid);
   }
 
-  const std::vector<PrimInfo> &info_;
+  std::vector<PrimInfo> &recs_;
+  std::vector<PrimInfo> tmp_;
   int bins_;
   uint32_t leaf_max_;
   LogicalBVH *out_;
@@ -348,51 +403,59 @@ inline void tri_verts(const BuildInput &in, uint64_t t, const float **v0, const 
 
 void build_logical(const BuildInput &in, uint32_t bins, uint32_t leaf_max, LogicalBVH *out) {
   const uint64_t n = in.n_tris;
-  std::vector<PrimInfo> info(n);
   std::vector<uint8_t> ok(n);
 #pragma omp parallel for schedule(static)
   for (long long t = 0; t < (long long)n; ++t) {
     const float *v0, *v1, *v2;
     tri_verts(in, (uint64_t)t, &v0, &v1, &v2);
     ok[t] = finite_tri(v0, v1, v2);
-    PrimInfo &q = info[t];
+  }
+  // records of the finite triangles, in id order
+  std::vector<uint32_t> pos(n + 1, 0);
+  for (uint64_t t = 0; t < n; ++t) pos[t + 1] = pos[t] + ok[t];
+  std::vector<PrimInfo> recs(pos[n]);
+#pragma omp parallel for schedule(static)
+  for (long long t = 0; t < (long long)n; ++t) {
+    if (!ok[t]) continue;
+    const float *v0, *v1, *v2;
+    tri_verts(in, (uint64_t)t, &v0, &v1, &v2);
+    PrimInfo &q = recs[pos[t]];
     for (int a = 0; a < 3; ++a) {
       q.lo[a] = std::min(v0[a], std::min(v1[a], v2[a]));
       q.hi[a] = std::max(v0[a], std::max(v1[a], v2[a]));
       q.c[a] = (v0[a] + v1[a] + v2[a]) * (1.0f / 3.0f);
     }
+    q.id = (uint32_t)t;
   }
-  out->prims.clear();
-  out->prims.reserve(n);
-  for (uint64_t t = 0; t < n; ++t)
-    if (ok[t]) out->prims.push_back((uint32_t)t);
-  SahBuilder b(info, bins, leaf_max, out);
+  SahBuilder b(recs, bins, leaf_max, out);
   b.run();
 }
 
 // ------------------------------------------------------------ node orders
 namespace {
 
-// Abstract tree of physical nodes: kids[i] lists the physical-node children
-// of node i (in slot order); area[i] its surface area. Node 0 is the root.
+// Abstract tree of physical nodes in CSR form: the physical-node children of
+// node i (in slot order) are kid[off[i] .. off[i+1]); area[i] is its surface
+// area. Node 0 is the root.
 struct OrderTree {
-  std::vector<std::vector<uint32_t>> kids;
+  std::vector<uint32_t> off, kid;
   std::vector<float> area;
+  size_t size() const { return area.size(); }
+  uint32_t nk(uint32_t i) const { return off[i + 1] - off[i]; }
+  const uint32_t *kids(uint32_t i) const { return kid.data() + off[i]; }
 };
 
 std::vector<uint32_t> order_nodes(const OrderTree &t, uint32_t order, bool group_siblings,
                                   uint32_t stride, uint32_t treelet_bytes) {
-  const size_t n = t.kids.size();
+  const size_t n = t.size();
   std::vector<uint32_t> out;
   out.reserve(n);
   if (n == 0) return out;
   if (order == ORDER_BFS) {
-    std::deque<uint32_t> q{0};
-    while (!q.empty()) {
-      uint32_t x = q.front();
-      q.pop_front();
-      out.push_back(x);
-      for (uint32_t c : t.kids[x]) q.push_back(c);
+    out.push_back(0);
+    for (size_t h = 0; h < out.size(); ++h) {
+      const uint32_t x = out[h];
+      for (uint32_t k = 0; k < t.nk(x); ++k) out.push_back(t.kids(x)[k]);
     }
     return out;
   }
@@ -400,18 +463,18 @@ std::vector<uint32_t> order_nodes(const OrderTree &t, uint32_t order, bool group
     std::vector<uint32_t> st{0};
     if (!group_siblings) {
       while (!st.empty()) {
-        uint32_t x = st.back();
+        const uint32_t x = st.back();
         st.pop_back();
         out.push_back(x);
-        for (size_t k = t.kids[x].size(); k-- > 0;) st.push_back(t.kids[x][k]);
+        for (uint32_t k = t.nk(x); k-- > 0;) st.push_back(t.kids(x)[k]);
       }
     } else {
       out.push_back(0);
       while (!st.empty()) {
-        uint32_t x = st.back();
+        const uint32_t x = st.back();
         st.pop_back();
-        for (uint32_t c : t.kids[x]) out.push_back(c);
-        for (size_t k = t.kids[x].size(); k-- > 0;) st.push_back(t.kids[x][k]);
+        for (uint32_t k = 0; k < t.nk(x); ++k) out.push_back(t.kids(x)[k]);
+        for (uint32_t k = t.nk(x); k-- > 0;) st.push_back(t.kids(x)[k]);
       }
     }
     return out;
@@ -420,52 +483,56 @@ std::vector<uint32_t> order_nodes(const OrderTree &t, uint32_t order, bool group
   // node (or sibling group) of largest surface area while the cluster fits the
   // byte budget; what is left on the frontier seeds later clusters.
   using Item = std::pair<float, uint32_t>;
+  std::vector<Item> heap, rest;
+  auto push = [&](Item it) { heap.push_back(it); std::push_heap(heap.begin(), heap.end()); };
+  auto pop = [&]() { std::pop_heap(heap.begin(), heap.end()); Item it = heap.back(); heap.pop_back(); return it; };
+  std::deque<uint32_t> roots;
   if (!group_siblings) {
-    std::deque<uint32_t> roots{0};
+    roots.push_back(0);
     while (!roots.empty()) {
-      uint32_t r = roots.front();
+      const uint32_t r = roots.front();
       roots.pop_front();
-      std::priority_queue<Item> fr;
+      heap.clear();
       out.push_back(r);
       uint32_t bytes = stride;
-      for (uint32_t c : t.kids[r]) fr.push({t.area[c], c});
-      while (!fr.empty() && bytes + stride <= treelet_bytes) {
-        uint32_t c = fr.top().second;
-        fr.pop();
+      for (uint32_t k = 0; k < t.nk(r); ++k) push({t.area[t.kids(r)[k]], t.kids(r)[k]});
+      while (!heap.empty() && bytes + stride <= treelet_bytes) {
+        const uint32_t c = pop().second;
         out.push_back(c);
         bytes += stride;
-        for (uint32_t g : t.kids[c]) fr.push({t.area[g], g});
+        for (uint32_t k = 0; k < t.nk(c); ++k) push({t.area[t.kids(c)[k]], t.kids(c)[k]});
       }
-      std::vector<Item> rest;
-      while (!fr.empty()) { rest.push_back(fr.top()); fr.pop(); }
+      rest.clear();
+      while (!heap.empty()) rest.push_back(pop());
       for (auto &it : rest) roots.push_back(it.second);
     }
     return out;
   }
-  // groups are identified by their parent node
+  // sibling groups, identified by their parent node
   out.push_back(0);
-  std::deque<uint32_t> roots;
-  if (!t.kids[0].empty()) roots.push_back(0);
+  if (t.nk(0) > 0) roots.push_back(0);
   while (!roots.empty()) {
-    uint32_t gp = roots.front();
+    const uint32_t gp = roots.front();
     roots.pop_front();
-    std::priority_queue<Item> fr;
+    heap.clear();
     uint32_t bytes = 0;
     auto emit = [&](uint32_t parent) {
-      for (uint32_t c : t.kids[parent]) out.push_back(c);
-      bytes += stride * (uint32_t)t.kids[parent].size();
-      for (uint32_t c : t.kids[parent])
-        if (!t.kids[c].empty()) fr.push({t.area[c], c});
+      for (uint32_t k = 0; k < t.nk(parent); ++k) out.push_back(t.kids(parent)[k]);
+      bytes += stride * t.nk(parent);
+      for (uint32_t k = 0; k < t.nk(parent); ++k) {
+        const uint32_t c = t.kids(parent)[k];
+        if (t.nk(c) > 0) push({t.area[c], c});
+      }
     };
     emit(gp);
-    while (!fr.empty()) {
-      uint32_t c = fr.top().second;
-      if (bytes + stride * (uint32_t)t.kids[c].size() > treelet_bytes) break;
-      fr.pop();
+    while (!heap.empty()) {
+      const uint32_t c = heap.front().second;
+      if (bytes + stride * t.nk(c) > treelet_bytes) break;
+      pop();
       emit(c);
     }
-    std::vector<Item> rest;
-    while (!fr.empty()) { rest.push_back(fr.top()); fr.pop(); }
+    rest.clear();
+    while (!heap.empty()) rest.push_back(pop());
     for (auto &it : rest) roots.push_back(it.second);
   }
   return out;
@@ -503,25 +570,58 @@ inline float u8_decode(uint32_t q, float scale, float origin) {
   return std::fma((float)q, scale, origin);
 }
 
-void emit_prims(const BuildInput &in, const LogicalBVH &lb, const LNode &leaf, HostBVH *out) {
-  for (uint32_t i = leaf.first; i < leaf.first + leaf.count; ++i) {
-    const uint32_t id = lb.prims[i];
+// Leaf entries [at, at + count) of a logical leaf, in the leaf's order.
+void emit_prims(const BuildInput &in, const LogicalBVH &lb, const LNode &leaf, HostBVH *out, uint32_t at) {
+  for (uint32_t k = 0; k < leaf.count; ++k) {
+    const uint32_t id = lb.prims[leaf.first + k];
     if (out->desc.prim_ref == REF_DIRECT) {
       const float *v0, *v1, *v2;
       tri_verts(in, id, &v0, &v1, &v2);
-      float rec[12] = {v0[0], v0[1], v0[2], 0.f, v1[0], v1[1], v1[2], 0.f, v2[0], v2[1], v2[2], 0.f};
+      float *rec = out->prim_direct.data() + 12 * (size_t)(at + k);
+      rec[0] = v0[0]; rec[1] = v0[1]; rec[2] = v0[2];
       std::memcpy(&rec[3], &id, 4);
-      out->prim_direct.insert(out->prim_direct.end(), rec, rec + 12);
+      rec[4] = v1[0]; rec[5] = v1[1]; rec[6] = v1[2]; rec[7] = 0.f;
+      rec[8] = v2[0]; rec[9] = v2[1]; rec[10] = v2[2]; rec[11] = 0.f;
     } else {
-      out->prim_ids.push_back(id);
+      out->prim_ids[at + k] = id;
     }
-    out->n_leaf_entries++;
   }
+}
+
+// Exclusive prefix sum in place; returns the total.
+uint64_t exclusive_scan(std::vector<uint32_t> &v) {
+  uint64_t acc = 0;
+  for (auto &x : v) {
+    const uint32_t c = x;
+    x = (uint32_t)acc;
+    acc += c;
+  }
+  return acc;
+}
+
+void alloc_prims(HostBVH *out, uint64_t entries) {
+  out->n_leaf_entries = (uint32_t)entries;
+  if (out->desc.prim_ref == REF_DIRECT) out->prim_direct.assign(12 * entries, 0.f);
+  else out->prim_ids.assign(entries, 0u);
+}
+
+// Stored-tree depth: parents come before children in every order.
+uint32_t tree_depth(const OrderTree &t, const std::vector<uint32_t> &ord) {
+  std::vector<uint32_t> depth(t.size(), 1);
+  uint32_t maxd = 1;
+  for (uint32_t x : ord)
+    for (uint32_t k = 0; k < t.nk(x); ++k) {
+      depth[t.kids(x)[k]] = depth[x] + 1;
+      maxd = std::max(maxd, depth[x] + 1);
+    }
+  return maxd;
 }
 
 }  // namespace
 
 // ------------------------------------------------------------ packing
+// Count pass (node order, leaf-entry offsets by prefix sum, one allocation per
+// buffer), then a parallel fill pass (App. F: rec_count, allocate, rec_build).
 scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_layout_desc &desc,
                       bool own_box, HostBVH *out, std::string *err) {
   out->desc = desc;
@@ -532,7 +632,8 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
   out->n_leaf_entries = 0;
   // vertex / index tables (used by indirect prims and by the backward pass)
   out->verts4.assign(4 * (size_t)in.n_verts, 0.f);
-  for (uint64_t v = 0; v < in.n_verts; ++v)
+#pragma omp parallel for schedule(static)
+  for (long long v = 0; v < (long long)in.n_verts; ++v)
     for (int k = 0; k < 3; ++k) out->verts4[4 * v + k] = in.verts[3 * v + k];
   if (in.indices) out->indices.assign(in.indices, in.indices + 3 * in.n_tris);
   const uint32_t W = desc.width;
@@ -548,46 +649,51 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
   if (own_box) {
     // ---- own-box binary nodes: every logical node is a physical node
     OrderTree t;
-    t.kids.resize(nl);
+    t.off.assign(nl + 1, 0);
     t.area.resize(nl);
-    for (size_t i = 0; i < nl; ++i) {
+    for (size_t i = 0; i < nl; ++i) t.off[i + 1] = t.off[i] + (lb.nodes[i].count == 0 ? 2u : 0u);
+    t.kid.resize(t.off[nl]);
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < (long long)nl; ++i) {
       t.area[i] = area_of(lb.nodes[i].box);
-      if (lb.nodes[i].count == 0) t.kids[i] = {lb.nodes[i].left, lb.nodes[i].right};
+      if (lb.nodes[i].count == 0) {
+        t.kid[t.off[i]] = lb.nodes[i].left;
+        t.kid[t.off[i] + 1] = lb.nodes[i].right;
+      }
     }
     const bool group = desc.child_ref == REF_INDIRECT;
     std::vector<uint32_t> ord = order_nodes(t, desc.order, group, kBinNodeBytes, desc.treelet_bytes);
     std::vector<uint32_t> phys(nl);
     for (size_t i = 0; i < ord.size(); ++i) phys[ord[i]] = (uint32_t)i;
-    // count pass: nodes = nl, prims = leaf entries; one allocation per buffer
+    // count pass: leaf entries per physical node, prefix-summed
+    std::vector<uint32_t> pbase(nl);
+    for (size_t pi = 0; pi < nl; ++pi) pbase[pi] = lb.nodes[ord[pi]].count;
+    alloc_prims(out, exclusive_scan(pbase));
     out->n_nodes = (uint32_t)nl;
     const bool soa = desc.box_layout == LAYOUT_SOA;
     out->node_stride = soa ? kBinBoxBytes : kBinNodeBytes;
     out->nodes.assign((size_t)nl * out->node_stride, 0);
     if (soa) out->nodes2.assign((size_t)nl * kBinRefBytes, 0);
-    // fill pass in physical order
-    std::vector<uint32_t> depth(nl, 1);
-    uint32_t maxd = 1;
-    for (size_t pi = 0; pi < nl; ++pi) {
-      const uint32_t li = ord[pi];
-      const LNode &nd = lb.nodes[li];
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (long long pi = 0; pi < (long long)nl; ++pi) {
+      const LNode &nd = lb.nodes[ord[pi]];
       const Box3 b = padded(nd.box);
       uint32_t ref, meta;
       if (nd.count > 0) {
-        ref = out->n_leaf_entries;
+        ref = pbase[pi];
         meta = bin_pack_meta(nd.count, 0);
-        emit_prims(in, lb, nd, out);
+        emit_prims(in, lb, nd, out, pbase[pi]);
       } else {
         const uint32_t l = phys[nd.left], r = phys[nd.right];
         if (desc.child_ref == REF_DIRECT) {
-          if (l != pi + 1) { *err = "DFS order violated"; return SCION_ERR_UNSUPPORTED_LAYOUT; }
+          bad |= l != (uint32_t)pi + 1;
           ref = r - (uint32_t)pi;
         } else {
-          if (r != l + 1) { *err = "siblings not contiguous"; return SCION_ERR_UNSUPPORTED_LAYOUT; }
+          bad |= r != l + 1;
           ref = l;
         }
         meta = bin_pack_meta(0, nd.axis);
-        depth[nd.left] = depth[nd.right] = depth[li] + 1;
-        maxd = std::max(maxd, depth[li] + 1);
       }
       uint8_t *p = out->nodes.data() + pi * out->node_stride;
       for (int a = 0; a < 3; ++a) {
@@ -598,14 +704,20 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
       put_u32(q, ref);
       put_u32(q + 4, meta);
     }
+    if (bad) {
+      *err = "node order violates the child reference encoding";
+      return SCION_ERR_UNSUPPORTED_LAYOUT;
+    }
     out->root_ref = 0;
-    out->depth = maxd;
-    out->stack_need = maxd;
+    out->depth = tree_depth(t, ord);
+    out->stack_need = out->depth;
     return SCION_OK;
   }
 
-  // ---- children-in-parent wide nodes: collapse the BVH2 to width W
+  // ---- children-in-parent wide nodes: collapse the BVH2 to width W by
+  // repeatedly opening the interior child of largest surface area
   std::vector<WNode> wn;
+  wn.reserve(nl / 2 + 1);
   std::vector<uint32_t> wide_of(nl, kEmptyRef);
   {
     std::vector<uint32_t> todo{0};
@@ -615,69 +727,88 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
       const uint32_t li = todo.back();
       todo.pop_back();
       const uint32_t wi = wide_of[li];
-      std::vector<uint32_t> ch;
-      if (lb.nodes[li].count > 0) {
-        ch.push_back(li);  // a leaf root: one-child wide root
-      } else {
-        ch = {lb.nodes[li].left, lb.nodes[li].right};
-        while (ch.size() < W) {
-          int best = -1;
-          float ba = -1.f;
-          for (size_t k = 0; k < ch.size(); ++k) {
-            const LNode &c = lb.nodes[ch[k]];
-            if (c.count == 0 && area_of(c.box) > ba) { ba = area_of(c.box); best = (int)k; }
-          }
-          if (best < 0) break;
-          const LNode &c = lb.nodes[ch[best]];
-          ch[best] = c.left;
-          ch.insert(ch.begin() + best + 1, c.right);
-        }
-      }
       WNode w{};
       w.lnode = li;
-      w.n = (uint32_t)ch.size();
-      for (size_t k = 0; k < ch.size(); ++k) {
-        w.child[k] = ch[k];
-        if (lb.nodes[ch[k]].count == 0 && ch[k] != li) {
-          wide_of[ch[k]] = (uint32_t)wn.size();
-          wn.push_back(WNode{});
-          todo.push_back(ch[k]);
+      if (lb.nodes[li].count > 0) {
+        w.n = 1;  // a leaf root: one-child wide root
+        w.child[0] = li;
+      } else {
+        w.n = 2;
+        w.child[0] = lb.nodes[li].left;
+        w.child[1] = lb.nodes[li].right;
+        while (w.n < W) {
+          int best = -1;
+          double ba = -1.0;
+          for (uint32_t k = 0; k < w.n; ++k) {
+            const LNode &c = lb.nodes[w.child[k]];
+            if (c.count == 0) {
+              const double a = box_area(c.box);
+              if (a > ba) { ba = a; best = (int)k; }
+            }
+          }
+          if (best < 0) break;
+          const LNode &c = lb.nodes[w.child[best]];
+          for (uint32_t k = w.n; k > (uint32_t)best + 1; --k) w.child[k] = w.child[k - 1];
+          w.child[best] = c.left;
+          w.child[best + 1] = c.right;
+          ++w.n;
+        }
+        for (uint32_t k = 0; k < w.n; ++k) {
+          if (lb.nodes[w.child[k]].count == 0) {
+            wide_of[w.child[k]] = (uint32_t)wn.size();
+            wn.push_back(WNode{});
+            todo.push_back(w.child[k]);
+          }
         }
       }
       wn[wi] = w;
     }
   }
   const size_t nw = wn.size();
+  if (nw >= kMaxNodes) { *err = "too many nodes"; return SCION_ERR_INVALID_ARG; }
   OrderTree t;
-  t.kids.resize(nw);
+  t.off.assign(nw + 1, 0);
   t.area.resize(nw);
   for (size_t i = 0; i < nw; ++i) {
+    uint32_t c = 0;
+    for (uint32_t k = 0; k < wn[i].n; ++k) c += lb.nodes[wn[i].child[k]].count == 0;
+    t.off[i + 1] = t.off[i] + c;
+  }
+  t.kid.resize(t.off[nw]);
+#pragma omp parallel for schedule(static)
+  for (long long i = 0; i < (long long)nw; ++i) {
     t.area[i] = area_of(lb.nodes[wn[i].lnode].box);
-    for (uint32_t k = 0; k < wn[i].n; ++k) {
-      const uint32_t c = wn[i].child[k];
-      if (lb.nodes[c].count == 0) t.kids[i].push_back(wide_of[c]);
-    }
+    uint32_t o = t.off[i];
+    for (uint32_t k = 0; k < wn[i].n; ++k)
+      if (lb.nodes[wn[i].child[k]].count == 0) t.kid[o++] = wide_of[wn[i].child[k]];
   }
   const uint32_t prec = desc.box_prec, soa = desc.box_layout, cref = desc.child_ref;
   const uint32_t stride = wide_node_stride(W, prec, cref);
   std::vector<uint32_t> ord = order_nodes(t, desc.order, cref == REF_INDIRECT, stride, desc.treelet_bytes);
   std::vector<uint32_t> phys(nw);
   for (size_t i = 0; i < ord.size(); ++i) phys[ord[i]] = (uint32_t)i;
-  if (nw >= kMaxNodes) { *err = "too many nodes"; return SCION_ERR_INVALID_ARG; }
+  // count pass: leaf entries per physical node (slot order), prefix-summed
+  std::vector<uint32_t> pbase(nw);
+  for (size_t pi = 0; pi < nw; ++pi) {
+    const WNode &w = wn[ord[pi]];
+    uint32_t c = 0;
+    for (uint32_t k = 0; k < w.n; ++k) c += lb.nodes[w.child[k]].count;
+    pbase[pi] = c;
+  }
+  alloc_prims(out, exclusive_scan(pbase));
   out->n_nodes = (uint32_t)nw;
   out->node_stride = stride;
   out->nodes.assign((size_t)nw * stride, 0);
-  std::vector<uint32_t> depth(nw, 1);
-  uint32_t maxd = 1;
   const uint32_t ref_off = wide_ref_offset(W, prec);
-  for (size_t pi = 0; pi < nw; ++pi) {
-    const uint32_t wi = ord[pi];
-    const WNode &w = wn[wi];
-    uint8_t *p = out->nodes.data() + pi * stride;
+  int bad = 0;  // 1: siblings not contiguous, 2: f16 enclosure, 4: u8 enclosure
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
+  for (long long pi = 0; pi < (long long)nw; ++pi) {
+    const WNode &w = wn[ord[pi]];
+    uint8_t *p = out->nodes.data() + (size_t)pi * stride;
     Box3 cb[8];
     for (uint32_t k = 0; k < w.n; ++k) cb[k] = padded(lb.nodes[w.child[k]].box);
     // references and leaf primitives (slot order)
-    uint32_t first_interior = kEmptyRef, first_prim = kEmptyRef, rank = 0;
+    uint32_t first_interior = kEmptyRef, rank = 0, at = pbase[pi];
     for (uint32_t k = 0; k < W; ++k) {
       uint32_t refv = kEmptyRef, meta = 0;
       if (k < w.n) {
@@ -685,21 +816,15 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
         if (c.count == 0) {
           const uint32_t cp = phys[wide_of[w.child[k]]];
           if (first_interior == kEmptyRef) first_interior = cp;
-          if (cref == REF_INDIRECT && cp != first_interior + rank) {
-            *err = "siblings not contiguous";
-            return SCION_ERR_UNSUPPORTED_LAYOUT;
-          }
+          if (cref == REF_INDIRECT && cp != first_interior + rank) bad |= 1;
           refv = ref_interior(cp);
           meta = kMetaInterior | rank;
           ++rank;
-          depth[wide_of[w.child[k]]] = depth[wi] + 1;
-          maxd = std::max(maxd, depth[wi] + 1);
         } else {
-          const uint32_t fp = out->n_leaf_entries;
-          if (first_prim == kEmptyRef) first_prim = fp;
-          refv = ref_leaf(fp, c.count);
+          refv = ref_leaf(at, c.count);
           meta = c.count;
-          emit_prims(in, lb, c, out);
+          emit_prims(in, lb, c, out, at);
+          at += c.count;
         }
       }
       if (cref == REF_DIRECT) put_u32(p + ref_off + 4 * k, refv);
@@ -707,7 +832,7 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
     }
     if (cref == REF_INDIRECT) {
       put_u32(p + ref_off, first_interior == kEmptyRef ? 0u : first_interior);
-      put_u32(p + ref_off + 4, first_prim == kEmptyRef ? 0u : first_prim);
+      put_u32(p + ref_off + 4, pbase[pi]);
     }
     // boxes
     if (prec == PREC_F32) {
@@ -724,7 +849,7 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
             h = c < 3 ? f32_to_f16_down(cb[k].lo[c]) : f32_to_f16_up(cb[k].hi[c - 3]);
             const float dec = f16_to_f32(h);
             const bool ok = c < 3 ? dec <= cb[k].lo[c] : dec >= cb[k].hi[c - 3];
-            if (!ok) { *err = "f16 enclosure"; return SCION_ERR_BAD_INPUT; }
+            if (!ok) bad |= 2;
           } else {
             h = c < 3 ? 0x7C00 : 0xFC00;  // +inf / -inf: empty
           }
@@ -743,14 +868,13 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
           mhi[a] = std::max(mhi[a], (double)cb[k].hi[a]);
         }
       }
-      double g = 0.0, mag = 0.0, ext = 0.0;
+      double mag = 0.0, ext = 0.0;
       for (int a = 0; a < 3; ++a) {
         mag = std::max(mag, std::max(std::fabs(mlo[a]), std::fabs(mhi[a])));
         ext = std::max(ext, mhi[a] - mlo[a]);
       }
-      g = std::ldexp(mag + ext, -20);
+      const double g = std::ldexp(mag + ext, -20);
       float origin[3], scale[3];
-      uint8_t ebyte[3];
       for (int a = 0; a < 3; ++a) {
         origin[a] = round_down_f32(mlo[a] - g);
         const double fhi = (double)round_up_f32(mhi[a] + g);
@@ -762,36 +886,36 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
           e = std::max(-126, ex - 2);
         }
         while (e < 127 && std::ldexp(255.0, e) < span) ++e;
-        ebyte[a] = (uint8_t)(e + 127);
         scale[a] = (float)std::ldexp(1.0, e);
         put_f32(p + 4 * a, origin[a]);
-        p[12 + a] = ebyte[a];
+        p[12 + a] = (uint8_t)(e + 127);
       }
       for (uint32_t k = 0; k < W; ++k)
         for (int a = 0; a < 3; ++a) {
           uint32_t qlo = 255, qhi = 0;
           if (k < w.n) {
             const double tlo = (double)cb[k].lo[a] - g, thi = (double)cb[k].hi[a] + g;
-            double fl = std::floor((tlo - origin[a]) / scale[a]);
-            double fh = std::ceil((thi - origin[a]) / scale[a]);
+            const double fl = std::floor((tlo - origin[a]) / scale[a]);
+            const double fh = std::ceil((thi - origin[a]) / scale[a]);
             qlo = (uint32_t)std::min(255.0, std::max(0.0, fl));
             qhi = (uint32_t)std::min(255.0, std::max(0.0, fh));
             while (qlo > 0 && (double)u8_decode(qlo, scale[a], origin[a]) > tlo) --qlo;
             while (qhi < 255 && (double)u8_decode(qhi, scale[a], origin[a]) < thi) ++qhi;
             if ((double)u8_decode(qlo, scale[a], origin[a]) > tlo ||
-                (double)u8_decode(qhi, scale[a], origin[a]) < thi) {
-              *err = "u8 enclosure";
-              return SCION_ERR_BAD_INPUT;
-            }
+                (double)u8_decode(qhi, scale[a], origin[a]) < thi)
+              bad |= 4;
           }
           p[wide_box_offset(W, prec, soa, k, a)] = (uint8_t)qlo;
           p[wide_box_offset(W, prec, soa, k, 3 + a)] = (uint8_t)qhi;
         }
     }
   }
+  if (bad & 1) { *err = "siblings not contiguous"; return SCION_ERR_UNSUPPORTED_LAYOUT; }
+  if (bad & 2) { *err = "f16 enclosure"; return SCION_ERR_BAD_INPUT; }
+  if (bad & 4) { *err = "u8 enclosure"; return SCION_ERR_BAD_INPUT; }
   out->root_ref = ref_interior(0);
-  out->depth = maxd;
-  out->stack_need = (W - 1) * maxd + 1;
+  out->depth = tree_depth(t, ord);
+  out->stack_need = (W - 1) * out->depth + 1;
   return SCION_OK;
 }
 

@@ -12,7 +12,9 @@
 // rays at a time from a global counter with one atomicAdd; each lane traces
 // one ray with a per-thread stack whose first entries live in shared memory
 // (strided by blockDim, conflict-free) and whose tail spills to local memory.
-// The current entry is always in registers.
+// The current entry is always in registers. (A variant that refilled idle
+// lanes mid-warp needed 74 instead of 64 registers, lost a quarter of the
+// occupancy and gained no SIMT efficiency; it was measured and dropped.)
 //
 // Arithmetic: the box test only has to be conservative; the triangle test is
 // pinned bit for bit (see tri_test). Translation units are compiled with
@@ -55,7 +57,8 @@ struct Counts {
 };
 
 constexpr int kLocalStack = 48;           // local-memory tail of the stack
-constexpr float kTMargin = 9.5367431640625e-07f;  // 2^-20, relative slab widening
+constexpr float kNearScale = 1.0f - 9.5367431640625e-07f;  // 1 - 2^-20: relative slab widening
+constexpr float kFarScale = 1.0f + 9.5367431640625e-07f;   // 1 + 2^-20
 constexpr uint32_t kErrStack = 5, kErrIter = 6;   // scion_status codes
 
 // ------------------------------------------------------------------ ray state
@@ -80,7 +83,8 @@ __device__ __forceinline__ float safe_rcp(float d) {
 }
 
 __device__ __forceinline__ void setup_ray(const float4 a, const float4 b, Ray &r) {
-  r.ox = a.x; r.oy = a.y; r.oz = a.z; r.tmin = a.w;
+  // hits behind the origin are never reported: tmin below 0 (or NaN) is 0
+  r.ox = a.x; r.oy = a.y; r.oz = a.z; r.tmin = a.w > 0.0f ? a.w : 0.0f;
   r.dx = b.x; r.dy = b.y; r.dz = b.z; r.tmax = b.w;
   r.rx = safe_rcp(r.dx); r.ry = safe_rcp(r.dy); r.rz = safe_rcp(r.dz);
   r.orx = __fmul_rn(r.ox, r.rx); r.ory = __fmul_rn(r.oy, r.ry); r.orz = __fmul_rn(r.oz, r.rz);
@@ -102,25 +106,42 @@ __device__ __forceinline__ void setup_ray(const float4 a, const float4 b, Ray &r
   r.Sz = __fdiv_rn(1.0f, dkz);
 }
 
-// Conservative slab test of one box against [tmin, tlim]; returns the widened
-// entry distance in tn. Planes are chosen near/far by direction sign; NaNs
-// from 0*inf are ignored by fminf/fmaxf (the axis then does not cull).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Conservative slab test from the six plane distances (near planes t0*, far
+// planes t1*) against [tmin, tlim]; returns the widened entry distance in tn.
+// Because tmin >= 0, scaling the entry distance by (1 - 2^-20) and the exit
+// distance by (1 + 2^-20) widens the interval by that relative amount wherever
+// the decision can change. NaNs from 0*inf are ignored by min/max (the axis
+// then does not cull).
+__device__ __forceinline__ bool slab_t(const Ray &r, float t0x, float t0y, float t0z, float t1x,
+                                       float t1y, float t1z, float tlim, float &tn) {
+  float a = fmax3(t0x, t0y, t0z) * kNearScale;
+  float b = fmin3(t1x, t1y, t1z) * kFarScale;
+  a = fmaxf(a, r.tmin);
+  b = fminf(b, tlim);
+  tn = a;
+  return a <= b;
+}
+
+// The same for a box given by its corners: near/far planes by direction sign,
+// distance = fma(plane, 1/d, -o/d).
 __device__ __forceinline__ bool slab(const Ray &r, float lox, float loy, float loz, float hix,
                                      float hiy, float hiz, float tlim, float &tn) {
   const float nx = r.nx ? hix : lox, fx = r.nx ? lox : hix;
   const float ny = r.ny ? hiy : loy, fy = r.ny ? loy : hiy;
   const float nz = r.nz ? hiz : loz, fz = r.nz ? loz : hiz;
-  const float t0x = fmaf(nx, r.rx, -r.orx), t1x = fmaf(fx, r.rx, -r.orx);
-  const float t0y = fmaf(ny, r.ry, -r.ory), t1y = fmaf(fy, r.ry, -r.ory);
-  const float t0z = fmaf(nz, r.rz, -r.orz), t1z = fmaf(fz, r.rz, -r.orz);
-  float a = fmaxf(fmaxf(t0x, t0y), t0z);
-  float b = fminf(fminf(t1x, t1y), t1z);
-  a = fmaf(-kTMargin, fabsf(a), a);
-  b = fmaf(kTMargin, fabsf(b), b);
-  a = fmaxf(a, r.tmin);
-  b = fminf(b, tlim);
-  tn = a;
-  return a <= b;
+  return slab_t(r, fmaf(nx, r.rx, -r.orx), fmaf(ny, r.ry, -r.ory), fmaf(nz, r.rz, -r.orz),
+                fmaf(fx, r.rx, -r.orx), fmaf(fy, r.ry, -r.ory), fmaf(fz, r.rz, -r.orz), tlim, tn);
 }
 
 // Pinned watertight ray/triangle test (Woop, Benthin & Wald, JCGT 2(1) 2013;
@@ -279,48 +300,116 @@ struct WideNode {
   }
 };
 
+// Per-lane traversal state that survives between steps, so that a lane can
+// finish its ray and take a new one while the rest of its warp is mid-ray.
+struct Lane {
+  Ray r;
+  Best b;
+  uint32_t cur;      // entry being processed (kEmptyRef: ray finished)
+  uint32_t steps;
+  uint32_t err;
+  bool found;        // any-hit result
+  unsigned long long rid;
+};
+
+// Next stacked entry that can still hold a closer hit (closest) or any
+// stacked entry (any-hit); kEmptyRef when the stack is exhausted.
+template <bool ANY>
+__device__ __forceinline__ uint32_t pop_next(Stack &st, float best_t, float &tn) {
+  while (st.sp > 0) {
+    const uint2 e = st.pop();
+    tn = __uint_as_float(e.y);
+    if (ANY || tn <= best_t) return e.x;
+  }
+  return kEmptyRef;
+}
+template <bool ANY>
+__device__ __forceinline__ uint32_t pop_next(Stack &st, float best_t) {
+  float tn;
+  return pop_next<ANY>(st, best_t, tn);
+}
+
+// Ascending sort of (entry distance, reference) pairs with a fixed
+// compare-exchange network: 1 comparator for 2 children, 5 for 4, 19 for 8
+// (Batcher's odd-even merge sort).
+__device__ __forceinline__ void cmpx(float *t, uint32_t *r, int i, int j) {
+  const bool sw = t[j] < t[i];
+  const float ti = sw ? t[j] : t[i], tj = sw ? t[i] : t[j];
+  const uint32_t ri = sw ? r[j] : r[i], rj = sw ? r[i] : r[j];
+  t[i] = ti; t[j] = tj; r[i] = ri; r[j] = rj;
+}
+
+template <int W>
+__device__ __forceinline__ void sort_children(float (&t)[W], uint32_t (&r)[W]) {
+  if constexpr (W == 2) {
+    cmpx(t, r, 0, 1);
+  } else if constexpr (W == 4) {
+    cmpx(t, r, 0, 1); cmpx(t, r, 2, 3); cmpx(t, r, 0, 2); cmpx(t, r, 1, 3); cmpx(t, r, 1, 2);
+  } else {
+    cmpx(t, r, 0, 1); cmpx(t, r, 2, 3); cmpx(t, r, 4, 5); cmpx(t, r, 6, 7);
+    cmpx(t, r, 0, 2); cmpx(t, r, 1, 3); cmpx(t, r, 4, 6); cmpx(t, r, 5, 7);
+    cmpx(t, r, 1, 2); cmpx(t, r, 5, 6);
+    cmpx(t, r, 0, 4); cmpx(t, r, 1, 5); cmpx(t, r, 2, 6); cmpx(t, r, 3, 7);
+    cmpx(t, r, 2, 4); cmpx(t, r, 3, 5);
+    cmpx(t, r, 1, 2); cmpx(t, r, 3, 4); cmpx(t, r, 5, 6);
+  }
+}
+
+// One step of the wide-node traversal: process the entry L.cur (an interior
+// node: test its W child boxes, push the hit ones far to near, continue with
+// the nearest; or a leaf: test its triangles), then pick the next entry.
 template <int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ bool trace_wide_ray(const TraceArgs &a, const Ray &r, Stack &st,
-                                               Best &b, uint32_t &err, Counts &cnt) {
+__device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st, Counts &cnt) {
   using N = WideNode<W, PREC, SOA, CREF>;
-  uint32_t cur = a.root_ref;
-  uint32_t steps = 0;
-  st.sp = 0;
-  while (cur != kEmptyRef) {
-    if (++steps > a.max_steps) { err = kErrIter; return false; }
-    if (ref_is_interior(cur)) {
-      if (STATS) cnt.nodes++;
-      const uint4 *np = a.nodes + (size_t)ref_node(cur) * (N::kStride / 16);
-      uint4 q[N::NQ];
+  const Ray &r = L.r;
+  const uint32_t cur = L.cur;
+  if (ref_is_interior(cur)) {
+    if (STATS) cnt.nodes++;
+    const uint4 *np = a.nodes + (size_t)ref_node(cur) * (N::kStride / 16);
+    uint4 q[N::NQ];
 #pragma unroll
-      for (int i = 0; i < N::NQ; ++i) q[i] = ldg4(np + i);
-      // u8 frame: coordinate = fma(code, 2^e, origin)
-      float ox = 0.f, oy = 0.f, oz = 0.f, sx = 1.f, sy = 1.f, sz = 1.f;
+    for (int i = 0; i < N::NQ; ++i) q[i] = ldg4(np + i);
+    // u8 frame: coordinate = origin + code * 2^e, folded into the plane
+    // distance t = fma(code, 2^e / d, (origin - o) / d) per axis
+    float ax = 0.f, bx = 0.f, ay = 0.f, by = 0.f, az = 0.f, bz = 0.f;
+    if (PREC == PREC_U8) {
+      ax = __uint_as_float((q[0].w & 0xFFu) << 23) * r.rx;
+      ay = __uint_as_float(((q[0].w >> 8) & 0xFFu) << 23) * r.ry;
+      az = __uint_as_float(((q[0].w >> 16) & 0xFFu) << 23) * r.rz;
+      bx = fmaf(__uint_as_float(q[0].x), r.rx, -r.orx);
+      by = fmaf(__uint_as_float(q[0].y), r.ry, -r.ory);
+      bz = fmaf(__uint_as_float(q[0].z), r.rz, -r.orz);
+    }
+    const float tlim = ANY ? r.tmax : fminf(r.tmax, L.b.t);
+    uint32_t cref[W];
+    float ctn[W];
+    uint32_t base_node = 0, base_prim = 0, leaf_acc = 0;
+    if (CREF == REF_INDIRECT) {
+      base_node = qword(q, N::kRefOff / 4);
+      base_prim = qword(q, N::kRefOff / 4 + 1);
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      uint32_t ref;
+      if (CREF == REF_DIRECT) {
+        ref = qword(q, N::kRefOff / 4 + k);
+      } else {
+        const uint32_t m = (qword(q, N::kRefOff / 4 + 2 + (k >> 2)) >> ((k & 3) * 8)) & 0xFFu;
+        if (m == 0) ref = kEmptyRef;
+        else if (m & kMetaInterior) ref = ref_interior(base_node + (m & 0x7Fu));
+        else { ref = ref_leaf(base_prim + leaf_acc, m); leaf_acc += m; }
+      }
+      float tn;
+      bool hit;
       if (PREC == PREC_U8) {
-        ox = __uint_as_float(q[0].x); oy = __uint_as_float(q[0].y); oz = __uint_as_float(q[0].z);
-        sx = __uint_as_float((q[0].w & 0xFFu) << 23);
-        sy = __uint_as_float(((q[0].w >> 8) & 0xFFu) << 23);
-        sz = __uint_as_float(((q[0].w >> 16) & 0xFFu) << 23);
-      }
-      const float tlim = ANY ? r.tmax : fminf(r.tmax, b.t);
-      uint32_t cref[W];
-      float ctn[W];
-      uint32_t base_node = 0, base_prim = 0, leaf_acc = 0;
-      if (CREF == REF_INDIRECT) {
-        base_node = qword(q, N::kRefOff / 4);
-        base_prim = qword(q, N::kRefOff / 4 + 1);
-      }
-#pragma unroll
-      for (int k = 0; k < W; ++k) {
-        uint32_t ref;
-        if (CREF == REF_DIRECT) {
-          ref = qword(q, N::kRefOff / 4 + k);
-        } else {
-          const uint32_t m = (qword(q, N::kRefOff / 4 + 2 + (k >> 2)) >> ((k & 3) * 8)) & 0xFFu;
-          if (m == 0) ref = kEmptyRef;
-          else if (m & kMetaInterior) ref = ref_interior(base_node + (m & 0x7Fu));
-          else { ref = ref_leaf(base_prim + leaf_acc, m); leaf_acc += m; }
-        }
+        const uint32_t lx = N::raw(q, k, 0), ly = N::raw(q, k, 1), lz = N::raw(q, k, 2);
+        const uint32_t hx = N::raw(q, k, 3), hy = N::raw(q, k, 4), hz = N::raw(q, k, 5);
+        const float nqx = (float)(r.nx ? hx : lx), fqx = (float)(r.nx ? lx : hx);
+        const float nqy = (float)(r.ny ? hy : ly), fqy = (float)(r.ny ? ly : hy);
+        const float nqz = (float)(r.nz ? hz : lz), fqz = (float)(r.nz ? lz : hz);
+        hit = slab_t(r, fmaf(nqx, ax, bx), fmaf(nqy, ay, by), fmaf(nqz, az, bz), fmaf(fqx, ax, bx),
+                     fmaf(fqy, ay, by), fmaf(fqz, az, bz), tlim, tn);
+      } else {
         float lo[3], hi[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -328,144 +417,141 @@ __device__ __forceinline__ bool trace_wide_ray(const TraceArgs &a, const Ray &r,
           if (PREC == PREC_F32) {
             lo[c] = __uint_as_float(ql);
             hi[c] = __uint_as_float(qh);
-          } else if (PREC == PREC_F16) {
+          } else {
             lo[c] = __half2float(__ushort_as_half((unsigned short)ql));
             hi[c] = __half2float(__ushort_as_half((unsigned short)qh));
-          } else {
-            const float o = c == 0 ? ox : (c == 1 ? oy : oz);
-            const float s = c == 0 ? sx : (c == 1 ? sy : sz);
-            lo[c] = fmaf((float)ql, s, o);
-            hi[c] = fmaf((float)qh, s, o);
           }
         }
-        float tn;
-        const bool hit = slab(r, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], tlim, tn) && ref != kEmptyRef;
-        cref[k] = hit ? ref : kEmptyRef;
-        ctn[k] = hit ? tn : __int_as_float(0x7f800000);
+        hit = slab(r, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], tlim, tn);
       }
-      if (!ANY && a.ordered) {
-        // ascending entry distance (odd-even transposition network)
-#pragma unroll
-        for (int pass = 0; pass < W; ++pass) {
-#pragma unroll
-          for (int k = pass & 1; k + 1 < W; k += 2) {
-            const bool sw = ctn[k + 1] < ctn[k];
-            const float t0 = sw ? ctn[k + 1] : ctn[k], t1 = sw ? ctn[k] : ctn[k + 1];
-            const uint32_t r0 = sw ? cref[k + 1] : cref[k], r1 = sw ? cref[k] : cref[k + 1];
-            ctn[k] = t0; ctn[k + 1] = t1; cref[k] = r0; cref[k + 1] = r1;
-          }
-        }
-      }
-      // push every hit child but the first, last one first; go on with the first
-      uint32_t next = kEmptyRef;
-      float next_tn = 0.f;
-#pragma unroll
-      for (int k = W - 1; k >= 0; --k) {
-        if (cref[k] == kEmptyRef) continue;
-        if (next != kEmptyRef && !st.push(next, next_tn)) { err = kErrStack; return false; }
-        next = cref[k];
-        next_tn = ctn[k];
-      }
-      if (next != kEmptyRef) { cur = next; continue; }
-    } else {
-      if (visit_leaf<ANY, STATS>(a, r, ref_leaf_first(cur), ref_leaf_count(cur), b, cnt)) return true;
+      hit = hit && ref != kEmptyRef;
+      cref[k] = hit ? ref : kEmptyRef;
+      ctn[k] = hit ? tn : __int_as_float(0x7f800000);
     }
-    // next stacked entry that can still hold a closer hit
-    cur = kEmptyRef;
-    while (st.sp > 0) {
-      const uint2 e = st.pop();
-      if (ANY || __uint_as_float(e.y) <= b.t) { cur = e.x; break; }
+    if (!ANY && a.ordered) sort_children<W>(ctn, cref);
+    // push every hit child but the first, last one first; go on with the first
+    uint32_t next = kEmptyRef;
+    float next_tn = 0.f;
+#pragma unroll
+    for (int k = W - 1; k >= 0; --k) {
+      if (cref[k] == kEmptyRef) continue;
+      if (next != kEmptyRef && !st.push(next, next_tn)) { L.err = kErrStack; L.cur = kEmptyRef; return; }
+      next = cref[k];
+      next_tn = ctn[k];
     }
+    L.cur = next != kEmptyRef ? next : pop_next<ANY>(st, L.b.t);
+  } else {
+    if (visit_leaf<ANY, STATS>(a, r, ref_leaf_first(cur), ref_leaf_count(cur), L.b, cnt)) {
+      L.found = true;
+      L.cur = kEmptyRef;
+      return;
+    }
+    L.cur = pop_next<ANY>(st, L.b.t);
   }
-  return false;
 }
 
-// ------------------------------------------------------------------ own-box node
+// One step of the own-box binary traversal (pbrt LinearBVH, Fig. 4b): test
+// the node's own box; a leaf tests its triangles, an interior node pushes its
+// far child (by the split axis and the ray direction) and continues near.
 template <int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ bool trace_bin_ray(const TraceArgs &a, const Ray &r, Stack &st,
-                                              Best &b, uint32_t &err, Counts &counts) {
-  if (a.n_nodes == 0) return false;
-  uint32_t cur = 0;
-  uint32_t steps = 0;
-  st.sp = 0;
-  while (cur != kEmptyRef) {
-    if (++steps > a.max_steps) { err = kErrIter; return false; }
-    if (STATS) counts.nodes++;
-    float lo0, lo1, lo2, hi0, hi1, hi2;
-    uint32_t ref, meta;
-    if (SOA) {
-      const uint2 *bp = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(a.nodes) +
-                                                        (size_t)cur * kBinBoxBytes);
-      const uint2 b0 = __ldg(bp), b1 = __ldg(bp + 1), b2 = __ldg(bp + 2);
-      const uint2 rm = __ldg(a.nodes2 + cur);
-      lo0 = __uint_as_float(b0.x); lo1 = __uint_as_float(b0.y); lo2 = __uint_as_float(b1.x);
-      hi0 = __uint_as_float(b1.y); hi1 = __uint_as_float(b2.x); hi2 = __uint_as_float(b2.y);
-      ref = rm.x; meta = rm.y;
-    } else {
-      const uint4 q0 = ldg4(a.nodes + 2 * (size_t)cur), q1 = ldg4(a.nodes + 2 * (size_t)cur + 1);
-      lo0 = __uint_as_float(q0.x); lo1 = __uint_as_float(q0.y); lo2 = __uint_as_float(q0.z);
-      hi0 = __uint_as_float(q0.w); hi1 = __uint_as_float(q1.x); hi2 = __uint_as_float(q1.y);
-      ref = q1.z; meta = q1.w;
-    }
-    const float tlim = ANY ? r.tmax : fminf(r.tmax, b.t);
-    float tn;
-    if (slab(r, lo0, lo1, lo2, hi0, hi1, hi2, tlim, tn)) {
-      const uint32_t cnt = bin_meta_count(meta);
-      if (cnt > 0) {
-        if (visit_leaf<ANY, STATS>(a, r, ref, cnt, b, counts)) return true;
-      } else {
-        const uint32_t l = CREF == REF_DIRECT ? cur + 1 : ref;
-        const uint32_t rr = CREF == REF_DIRECT ? cur + ref : ref + 1;
-        const uint32_t ax = bin_meta_axis(meta);
-        const bool neg = ax == 0 ? r.nx : (ax == 1 ? r.ny : r.nz);
-        const bool swap = !ANY && a.ordered && neg;
-        if (!st.push(swap ? l : rr, 0.0f)) { err = kErrStack; return false; }
-        cur = swap ? rr : l;
-        continue;
-      }
-    }
-    cur = st.sp > 0 ? st.pop().x : kEmptyRef;
+__device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, Stack &st, Counts &cnt) {
+  const Ray &r = L.r;
+  const uint32_t cur = L.cur;
+  if (STATS) cnt.nodes++;
+  float lo0, lo1, lo2, hi0, hi1, hi2;
+  uint32_t ref, meta;
+  if (SOA) {
+    const uint2 *bp = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(a.nodes) +
+                                                      (size_t)cur * kBinBoxBytes);
+    const uint2 b0 = __ldg(bp), b1 = __ldg(bp + 1), b2 = __ldg(bp + 2);
+    const uint2 rm = __ldg(a.nodes2 + cur);
+    lo0 = __uint_as_float(b0.x); lo1 = __uint_as_float(b0.y); lo2 = __uint_as_float(b1.x);
+    hi0 = __uint_as_float(b1.y); hi1 = __uint_as_float(b2.x); hi2 = __uint_as_float(b2.y);
+    ref = rm.x; meta = rm.y;
+  } else {
+    const uint4 q0 = ldg4(a.nodes + 2 * (size_t)cur), q1 = ldg4(a.nodes + 2 * (size_t)cur + 1);
+    lo0 = __uint_as_float(q0.x); lo1 = __uint_as_float(q0.y); lo2 = __uint_as_float(q0.z);
+    hi0 = __uint_as_float(q0.w); hi1 = __uint_as_float(q1.x); hi2 = __uint_as_float(q1.y);
+    ref = q1.z; meta = q1.w;
   }
-  return false;
+  const float tlim = ANY ? r.tmax : fminf(r.tmax, L.b.t);
+  float tn;
+  if (slab(r, lo0, lo1, lo2, hi0, hi1, hi2, tlim, tn)) {
+    const uint32_t n = bin_meta_count(meta);
+    if (n > 0) {
+      if (visit_leaf<ANY, STATS>(a, r, ref, n, L.b, cnt)) {
+        L.found = true;
+        L.cur = kEmptyRef;
+        return;
+      }
+    } else {
+      const uint32_t l = CREF == REF_DIRECT ? cur + 1 : ref;
+      const uint32_t rr = CREF == REF_DIRECT ? cur + ref : ref + 1;
+      const uint32_t ax = bin_meta_axis(meta);
+      const bool neg = ax == 0 ? r.nx : (ax == 1 ? r.ny : r.nz);
+      const bool swap = !ANY && a.ordered && neg;
+      if (!st.push(swap ? l : rr, 0.0f)) { L.err = kErrStack; L.cur = kEmptyRef; return; }
+      L.cur = swap ? rr : l;
+      return;
+    }
+  }
+  L.cur = st.sp > 0 ? st.pop().x : kEmptyRef;
 }
 
 // ------------------------------------------------------------------ kernel body
+// Trace one ray to completion with the layout's step function.
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
+__device__ __forceinline__ void trace_lane(const TraceArgs &a, Lane &L, Stack &st, Counts &cnt) {
+  while (L.cur != kEmptyRef) {
+    if (++L.steps > a.max_steps) {
+      L.err = kErrIter;
+      L.cur = kEmptyRef;
+      break;
+    }
+    if constexpr (OWN) step_bin<SOA, CREF, ANY, STATS>(a, L, st, cnt);
+    else step_wide<W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
+  }
+}
+
+// Persistent warps: each warp takes 32 consecutive rays with one atomicAdd on
+// the global counter, every lane traces one of them to completion, repeat.
 template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
 __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
-  Counts cnt;
-  uint32_t n_rays = 0;
   extern __shared__ uint2 smem_stack[];
   Stack st;
   st.sh = smem_stack + threadIdx.x;
   st.stride = blockDim.x;
   st.cap_sh = (int)a.smem_stack;
-  const int lane = threadIdx.x & 31;
+  st.sp = 0;
+  Counts cnt;
+  uint32_t n_rays = 0;
+  const uint32_t lane = threadIdx.x & 31u;
   while (true) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.work, 32ull);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     if (base >= a.n) break;
     const unsigned long long rid = base + lane;
-    if (rid < a.n) {
-      Ray r;
-      setup_ray(ldg4f(a.rays + 2 * rid), ldg4f(a.rays + 2 * rid + 1), r);
-      Best b{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_MISS};
-      uint32_t err = 0;
-      bool found = false;
-      if (STATS) n_rays++;
-      if constexpr (OWN) {
-        found = trace_bin_ray<SOA, CREF, ANY, STATS>(a, r, st, b, err, cnt);
-      } else {
-        if (a.root_ref != kEmptyRef) found = trace_wide_ray<W, PREC, SOA, CREF, ANY, STATS>(a, r, st, b, err, cnt);
-      }
-      if (err) atomicCAS(a.status, 0u, err);
-      if (ANY) {
-        static_cast<uint32_t *>(a.out)[rid] = err ? SCION_PRIM_ERROR : (found ? 1u : 0u);
-      } else {
-        if (err) b = Best{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_ERROR};
-        static_cast<uint4 *>(a.out)[rid] =
-            make_uint4(__float_as_uint(b.t), __float_as_uint(b.u), __float_as_uint(b.v), b.id);
-      }
+    if (rid >= a.n) continue;
+    Lane L;
+    L.rid = rid;
+    setup_ray(ldg4f(a.rays + 2 * rid), ldg4f(a.rays + 2 * rid + 1), L.r);
+    L.b = Best{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_MISS};
+    L.steps = 0;
+    L.err = 0;
+    L.found = false;
+    st.sp = 0;
+    if constexpr (OWN) L.cur = a.n_nodes > 0 ? 0u : kEmptyRef;
+    else L.cur = a.root_ref;
+    if (STATS) n_rays++;
+    trace_lane<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
+    if (L.err) atomicCAS(a.status, 0u, L.err);
+    if (ANY) {
+      static_cast<uint32_t *>(a.out)[rid] = L.err ? SCION_PRIM_ERROR : (L.found ? 1u : 0u);
+    } else {
+      if (L.err) L.b = Best{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_ERROR};
+      static_cast<uint4 *>(a.out)[rid] =
+          make_uint4(__float_as_uint(L.b.t), __float_as_uint(L.b.u), __float_as_uint(L.b.v), L.b.id);
     }
   }
   if (STATS) {

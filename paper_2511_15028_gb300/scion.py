@@ -98,10 +98,18 @@ def lib():
         P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         L.scion_build.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), P, ctypes.POINTER(P)]
         L.scion_bvh_info.argtypes = [P, P, P, P, P]
+        L.scion_build_many.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), U32, P, ctypes.POINTER(P)]
         L.scion_trace_closest.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
         L.scion_trace_any.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
         L.scion_get_status.argtypes = [P, P, P]
         L.scion_trace_stats.argtypes = [P, P, U64, U32, P, ctypes.POINTER(TraceParams), P, P]
+        L.scion_trace_backward.argtypes = [P, P, P, P, U64, P, P, P]
+        L.scion_batch_create.argtypes = [P, P, P, P, U32, P, P, ctypes.POINTER(P)]
+        L.scion_batch_launch.argtypes = [P, P]
+        L.scion_batch_info.argtypes = [P, P, P]
+        L.scion_batch_destroy.argtypes = [P]
+        L.scion_batch_destroy.restype = None
+        L.scion_trace_batched.argtypes = [P, P, P, P, U32, P, P]
         L.scion_destroy.argtypes = [P]
         L.scion_destroy.restype = None
         L.scion_status_string.argtypes = [I]
@@ -116,8 +124,9 @@ def lib():
         L.scion_debug_f16_round.restype = U32
         L.scion_debug_f16_decode.argtypes = [U32]
         L.scion_debug_f16_decode.restype = ctypes.c_float
-        for name in ("scion_build", "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
-                     "scion_trace_stats",
+        for name in ("scion_build", "scion_build_many", "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
+                     "scion_trace_stats", "scion_trace_backward", "scion_batch_create",
+                     "scion_batch_launch", "scion_batch_info", "scion_trace_batched",
                      "scion_get_status", "scion_debug_build_host", "scion_debug_host_stats",
                      "scion_debug_host_decode"):
             getattr(L, name).restype = I
@@ -192,6 +201,32 @@ def scion_build(verts, desc: LayoutDesc, indices=None, stream=None) -> BVH:
     return BVH(h, nt, nv, desc)
 
 
+def scion_build_many(verts, descs, indices=None, stream=None):
+    """Several layouts of one scene from a single logical build: list of BVH."""
+    import torch
+    keep = []
+
+    def ptr(x, dtype):
+        if x is None:
+            return None, 0
+        if isinstance(x, torch.Tensor):
+            t = x.contiguous()
+            keep.append(t)
+            return ctypes.c_void_p(t.data_ptr()), t.shape[0]
+        a = _as_np(x, dtype)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.c_void_p), a.shape[0]
+
+    vp, nv = ptr(verts, np.float32)
+    ip, nt = ptr(indices, np.uint32)
+    if indices is None:
+        nt = nv // 3
+    arr = (LayoutDesc * len(descs))(*descs)
+    hs = (ctypes.c_void_p * len(descs))()
+    _check(lib().scion_build_many(vp, nv, ip, nt, arr, len(descs), _stream_ptr(stream), hs), "scion_build_many")
+    return [BVH(ctypes.c_void_p(h), nt, nv, d) for h, d in zip(hs, descs)]
+
+
 def scion_bvh_info(bvh: BVH) -> dict:
     nb, pb = ctypes.c_uint64(), ctypes.c_uint64()
     d, n = ctypes.c_uint32(), ctypes.c_uint32()
@@ -248,6 +283,121 @@ def scion_trace_stats(bvh: BVH, rays, query: int = 0, params=None, stream=None):
                                    ctypes.c_void_p(out.data_ptr()), _params(params), _stream_ptr(stream),
                                    ctypes.c_void_p(cnt.data_ptr())), "scion_trace_stats")
     return out, cnt
+
+
+def scion_trace_backward(bvh: BVH, rays, hits, grad_tuv, grad_verts=None, grad_rays=None,
+                         want_ray_grads: bool = True, stream=None):
+    """Backward pass: returns (grad_verts float32 [n_verts, 3] (accumulated
+    into if given), grad_rays float32 [n, 8] or None)."""
+    import torch
+    n = rays.shape[0]
+    dev = rays.device
+    g = grad_tuv.contiguous().float()
+    if grad_verts is None:
+        grad_verts = torch.zeros((bvh.n_verts, 3), dtype=torch.float32, device=dev)
+    if grad_rays is None and want_ray_grads:
+        grad_rays = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    _check(lib().scion_trace_backward(bvh.handle, ctypes.c_void_p(rays.data_ptr()),
+                                      ctypes.c_void_p(hits.data_ptr()), ctypes.c_void_p(g.data_ptr()), n,
+                                      ctypes.c_void_p(grad_verts.data_ptr()),
+                                      None if grad_rays is None else ctypes.c_void_p(grad_rays.data_ptr()),
+                                      _stream_ptr(stream)), "scion_trace_backward")
+    return grad_verts, grad_rays
+
+
+def _trace_fn():
+    import torch
+
+    class TraceFn(torch.autograd.Function):
+        """Differentiable closest hit: (verts, rays) -> (t, u, v, prim).
+
+        The forward traces with the BVH built from `verts` (the caller keeps the
+        two consistent); the backward keeps every ray's hit triangle fixed and
+        returns dL/dverts and dL/drays (the ray's tmin/tmax get zero)."""
+
+        @staticmethod
+        def forward(ctx, verts, rays, bvh):
+            hits = scion_trace_closest(bvh, rays.detach().contiguous())
+            ctx.save_for_backward(rays, hits)
+            ctx.bvh = bvh
+            f = hits.view(torch.float32)
+            prim = hits[:, 3]
+            ctx.mark_non_differentiable(prim)
+            return f[:, 0].clone(), f[:, 1].clone(), f[:, 2].clone(), prim.clone()
+
+        @staticmethod
+        def backward(ctx, gt, gu, gv, _gp):
+            rays, hits = ctx.saved_tensors
+            n = rays.shape[0]
+            z = lambda x: x if x is not None else torch.zeros(n, device=rays.device)  # noqa: E731
+            g = torch.stack([z(gt), z(gu), z(gv)], -1).contiguous()
+            gverts, grays = scion_trace_backward(ctx.bvh, rays.detach().contiguous(), hits, g,
+                                                 want_ray_grads=ctx.needs_input_grad[1])
+            return (gverts if ctx.needs_input_grad[0] else None,
+                    grays if ctx.needs_input_grad[1] else None, None)
+
+    return TraceFn
+
+
+_TRACE_FN = None
+
+
+def trace_fn():
+    """The torch.autograd.Function class for differentiable closest hits."""
+    global _TRACE_FN
+    if _TRACE_FN is None:
+        _TRACE_FN = _trace_fn()
+    return _TRACE_FN
+
+
+class Batch:
+    """Many scenes in one launch (scion_batch_*). The rays and hit tensors
+    must stay alive and in place while the batch exists; launch() allocates
+    nothing and may be captured in a CUDA graph."""
+
+    def __init__(self, bvhs, rays, hits=None, params=None, stream=None):
+        import torch
+        self.bvhs = list(bvhs)
+        self.rays = [r.contiguous() for r in rays]
+        self.hits = hits if hits is not None else [
+            torch.empty((r.shape[0], 4), dtype=torch.int32, device=r.device) for r in self.rays]
+        m = len(self.bvhs)
+        hb = (ctypes.c_void_p * m)(*[b.handle.value if isinstance(b.handle, ctypes.c_void_p) else b.handle
+                                     for b in self.bvhs])
+        rp = (ctypes.c_void_p * m)(*[r.data_ptr() for r in self.rays])
+        n = (ctypes.c_uint64 * m)(*[r.shape[0] for r in self.rays])
+        hp = (ctypes.c_void_p * m)(*[h.data_ptr() for h in self.hits])
+        pp = None
+        if params is not None:
+            pp = (TraceParams * m)(*[p if isinstance(p, TraceParams) else TraceParams(**(p or {}))
+                                     for p in params])
+        self._keep = (hb, rp, n, hp, pp)
+        self.handle = ctypes.c_void_p()
+        _check(lib().scion_batch_create(hb, rp, n, hp, m, pp, _stream_ptr(stream), ctypes.byref(self.handle)),
+               "scion_batch_create")
+
+    def launch(self, stream=None):
+        _check(lib().scion_batch_launch(self.handle, _stream_ptr(stream)), "scion_batch_launch")
+        return self.hits
+
+    def info(self):
+        a, b = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().scion_batch_info(self.handle, ctypes.byref(a), ctypes.byref(b)), "scion_batch_info")
+        return {"batched_scenes": a.value, "plain_scenes": b.value}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.scion_batch_destroy(self.handle)
+            self.handle = None
+
+
+def scion_trace_batched(bvhs, rays, hits=None, params=None, stream=None):
+    """One-shot batched closest hit over many scenes; returns the hit tensors."""
+    b = Batch(bvhs, rays, hits, params, stream)
+    b.launch(stream)
+    import torch
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return b.hits
 
 
 def scion_get_status(bvh: BVH, stream=None) -> int:

@@ -1,0 +1,78 @@
+"""Full-size parity in the launch configuration the benchmark times (default
+trace parameters): the coherent+incoherent workload (1,373,138 triangles,
+1920x1080 primary rays plus bounce and shadow rays) on all swept layouts, and
+the incoherent 2^23-triangle soup with 2^23 random rays (closest hit and
+any hit with tmax 0.05). Config-2 outputs are all compared with the CPU
+oracle's BVH2 (bounce and shadow rays come from its own primary hits);
+config-3 outputs on a sample, against brute force."""
+import numpy as np
+import pytest
+
+from paper_2511_15028_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sc_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_15028_gb300 import build as b
+    b.build()
+    from paper_2511_15028_gb300 import scion
+    scion.lib()
+    return scion
+
+
+def _cmp(scion, got_i32, exp, what):
+    g = got_i32.cpu().numpy().view(np.uint32).reshape(-1, 4)
+    e = np.ascontiguousarray(exp).view(np.uint32).reshape(-1, 4)
+    bad = np.where(np.any(g != e, axis=1))[0]
+    assert bad.size == 0, f"{what}: {bad.size} of {len(e)} differ, e.g. {bad[:5]}"
+
+
+def test_config2_full_size_all_layouts(sc_mod, oracle_mod):
+    scion = sc_mod
+    sc = scenes.config2_scene()
+    assert sc.n_tris == 1_373_138
+    prim = scenes.config2_primary()
+    ob = oracle_mod.BVH2(sc.triangles())
+    hp = ob.closest(prim)
+    bounce = scenes.bounce_rays(sc, prim, hp["t"], hp["u"], hp["v"], hp["prim"], seed=2002)
+    shadow = scenes.shadow_rays(sc, prim, hp["t"], hp["u"], hp["v"], hp["prim"])
+    hb = ob.closest(bounce)
+    hs = ob.any(shadow)
+    d = [torch.from_numpy(r).cuda() for r in (prim, bounce, shadow)]
+    for name, desc in scion.sweep_layouts().items():
+        bvh = scion.scion_build(sc.verts, desc, sc.indices)
+        _cmp(scion, scion.scion_trace_closest(bvh, d[0]), hp, name + " primary")
+        _cmp(scion, scion.scion_trace_closest(bvh, d[1]), hb, name + " bounce")
+        occ = scion.scion_trace_any(bvh, d[2]).cpu().numpy().astype(np.uint32)
+        assert np.array_equal(occ, hs), name + " shadow"
+        assert scion.scion_get_status(bvh) == 0
+
+
+def test_config3_full_size(sc_mod, oracle_mod):
+    """All 2^23 rays are traced on the GPU; 256 sampled rays are checked
+    against brute force over all 2^23 triangles (the definition itself)."""
+    scion = sc_mod
+    sc = scenes.config3_scene()
+    assert sc.n_tris == 1 << 23
+    rays = scenes.config3_rays()
+    short = rays.copy()
+    short[:, 7] = 0.05
+    pick = np.sort(np.random.default_rng(5).choice(rays.shape[0], 256, replace=False))
+    tris = sc.verts.reshape(-1, 9)
+    exp = oracle_mod.closest_brute(tris, rays[pick])
+    eocc = oracle_mod.any_brute(tris, short[pick])
+    assert 0.3 < (exp["prim"] != 0xFFFFFFFF).mean() and 0.02 < eocc.mean() < 0.98
+    d, ds = torch.from_numpy(rays).cuda(), torch.from_numpy(short).cuda()
+    for name, desc in scion.sweep_layouts().items():
+        bvh = scion.scion_build(sc.verts, desc)
+        got = scion.scion_trace_closest(bvh, d)[torch.from_numpy(pick).cuda()]
+        _cmp(scion, got, exp, name + " closest")
+        occ = scion.scion_trace_any(bvh, ds).cpu().numpy().astype(np.uint32)[pick]
+        assert np.array_equal(occ, eocc), name + " any"
+        assert scion.scion_get_status(bvh) == 0
+        del bvh

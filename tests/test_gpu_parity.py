@@ -130,6 +130,11 @@ def test_edge_cases(sc_mod, oracle_mod):
     bad[5, 4:7] = [1, 0, 0]
     bad[6, 0:3] = [0.0, 0.0, 0.5]
     bad[6, 4:7] = [0, -1, 0]
+    bad[7, 3] = -np.inf  # tmin below zero counts as zero
+    bad[8, 3] = np.nan
+    bad[9, 0:3] = [0.1, 0.1, -1.0]  # below the surface looking up, tmin < 0
+    bad[9, 3] = -10.0
+    bad[9, 4:7] = [0, 0, 1]
     exp = oracle_mod.closest_brute(sc.triangles(), bad)
     for kw in ALL[::3]:
         b = sc_mod.scion_build(sc.verts, sc_mod.layout(**kw), sc.indices)

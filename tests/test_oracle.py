@@ -174,7 +174,7 @@ def test_intersector_against_exact_rational_arithmetic(oracle_mod):
         ray = np.concatenate([o, [-np.inf], d, [np.inf]]).astype(np.float32)
         inside, t, u, v, cond = _exact_inside(o, d, p)
         got = oracle_mod.intersect(ray, p)
-        if not inside or cond > 100:
+        if not inside or cond > 100 or float(t) <= 0:
             continue
         if min(float(u), float(v), 1 - float(u) - float(v)) < 1e-5 * cond:
             continue
@@ -205,7 +205,9 @@ def test_intersector_exact_miss_agreement(oracle_mod):
         w = 1 - u - v
         if min(u, v, w) < -1e-3:
             assert oracle_mod.intersect(ray, p) is None
-        elif min(u, v, w) > 1e-3:
+        elif min(u, v, w) > 1e-3 and t < -1e-3:
+            assert oracle_mod.intersect(ray, p) is None  # behind the origin
+        elif min(u, v, w) > 1e-3 and t > 1e-3:
             got = oracle_mod.intersect(ray, p)
             assert got is not None
             assert abs(got[0] - t) <= 1e-4 * max(1.0, abs(t))
