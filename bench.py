@@ -277,6 +277,73 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ incoherent (config 3)
+def pareto(points):
+    """Names on the footprint-vs-throughput Pareto front (smaller MB, higher Mrays/s)."""
+    front = []
+    for n, (mb, mr) in points.items():
+        if not any((mb2 <= mb and mr2 >= mr) and (mb2 < mb or mr2 > mr) for n2, (mb2, mr2) in points.items()):
+            front.append(n)
+    return sorted(front, key=lambda n: points[n][0])
+
+
+def bench_incoherent(scion, torch, steps, warmup, hbm_peak):
+    """2^23 random triangles and 2^23 random rays in the unit cube (BVH far
+    larger than L2): closest hit (tmax inf) and any hit (tmax 0.05) for every
+    swept layout, built from one logical BVH."""
+    from paper_2511_15028_gb300 import scenes
+    t0 = time.time()
+    sc = scenes.config3_scene()
+    rays = torch.from_numpy(scenes.config3_rays()).cuda()
+    short = rays.clone()
+    short[:, 7] = 0.05
+    gen_s = time.time() - t0
+    lays = scion.sweep_layouts()
+    t0 = time.time()
+    bvhs = scion.scion_build_many(sc.verts, list(lays.values()))
+    build_s = time.time() - t0
+    n = rays.shape[0]
+    hits = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    occ = torch.empty((n,), dtype=torch.int32, device="cuda")
+    out = {}
+    for (name, desc), bvh in zip(lays.items(), bvhs):
+        info = scion.scion_bvh_info(bvh)
+        _, cc = scion.scion_trace_stats(bvh, rays, 0)
+        _, ca = scion.scion_trace_stats(bvh, short, 1)
+        cc, ca = cc.cpu().numpy(), ca.cpu().numpy()
+        sn, st = node_load_bytes(desc), tri_load_bytes(desc, False)
+        alg = {"closest": int(cc[3]) * 48 + int(cc[0]) * sn + int(cc[2]) * st,
+               "any": int(ca[3]) * 36 + int(ca[0]) * sn + int(ca[2]) * st}
+        res = {}
+        for q, fn, r, o in (("closest", scion.scion_trace_closest, rays, hits),
+                            ("any", scion.scion_trace_any, short, occ)):
+            for _ in range(warmup):
+                fn(bvh, r, o)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn(bvh, r, o)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = trimmed_mean(ts)
+            gbs = alg[q] / (ms / 1e3) / 1e9
+            res[q] = {"ms": ms, "mrays_s": n / (ms / 1e3) / 1e6, "bytes_per_ray": alg[q] / n,
+                      "alg_gbs": gbs, "roofline_frac_of_measured_hbm": gbs / hbm_peak}
+        res["bvh_mb"] = (info["node_bytes"] + info["prim_bytes"]) / 1e6
+        res["nodes_per_ray"] = {"closest": float(cc[0]) / n, "any": float(ca[0]) / n}
+        res["tris_per_ray"] = {"closest": float(cc[2]) / n, "any": float(ca[2]) / n}
+        out[name] = res
+        scion.scion_destroy(bvh)
+    best = max(out, key=lambda k: out[k]["closest"]["mrays_s"])
+    return {"tris": sc.n_tris, "rays": n, "gen_s": round(gen_s, 1), "build_8_layouts_s": round(build_s, 1),
+            "layouts": out, "best_closest": best,
+            "pareto_closest": pareto({k: (v["bvh_mb"], v["closest"]["mrays_s"]) for k, v in out.items()}),
+            "pareto_any": pareto({k: (v["bvh_mb"], v["any"]["mrays_s"]) for k, v in out.items()})}
+
+
 # ------------------------------------------------------------------ batched (config 4)
 def bench_batched(scion, torch, steps, warmup, flush_buf, seed=1004):
     """64 uneven scenes, each with its own rays and autotuned layout: one
@@ -513,8 +580,9 @@ def main():
            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
     for v in results.values():
         v.pop("_bvh", None)
-    extra = {}
+    extra = {"pareto_coherent": pareto({k: (v["bvh_mb"], v["mrays_s"]) for k, v in results.items()})}
     if not args.no_extra:
+        extra["incoherent"] = bench_incoherent(scion, torch, args.steps, args.warmup, hbm_peak)
         extra["batched"] = bench_batched(scion, torch, args.steps, args.warmup, flush_buf)
         extra["backward"] = bench_backward(scion, torch, args.steps, args.warmup)
     cpu = None
