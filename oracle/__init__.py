@@ -41,6 +41,38 @@ def build(force: bool = False) -> str:
     return LIB_PATH
 
 
+def _bind(path):
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    U64 = ctypes.c_uint64
+    I = ctypes.c_int
+    L.oracle_intersect.argtypes = [P, P, P, P, P]
+    L.oracle_intersect.restype = I
+    L.oracle_closest_brute.argtypes = [P, U64, P, U64, P, I]
+    L.oracle_any_brute.argtypes = [P, U64, P, U64, P, I]
+    L.oracle_bvh_build.argtypes = [P, U64, I, I]
+    L.oracle_bvh_build.restype = P
+    L.oracle_bvh_closest.argtypes = [P, P, U64, P, I]
+    L.oracle_bvh_any.argtypes = [P, P, U64, P, I]
+    L.oracle_bvh_stats.argtypes = [P, P, P, P]
+    L.oracle_bvh_free.argtypes = [P]
+    L.oracle_grad.argtypes = [P, P, U64, P, P, P, U64, P, P]
+    L.oracle_grad_fd.argtypes = [P, P, U64, P, P, P, U64, ctypes.c_double, P, P]
+    L.oracle_plane_tuv.argtypes = [P, P, P, P, P, P]
+    L.oracle_plane_tuv.restype = I
+    L.oracle_max_threads.restype = I
+    return L
+
+
+def use_library(path):
+    """Swap in another build of oracle.c (the mutation tests use this to check
+    that planted mistakes fail the pins). Returns the previous library."""
+    global _lib
+    prev = _lib
+    _lib = _bind(path) if path else None
+    return prev
+
+
 def lib():
     global _lib
     if _lib is None:
