@@ -169,16 +169,44 @@ def flush_l2(buf):
     buf.zero_()
 
 
+FETCH_MODES = {"warp_batch": {}, "lane_fetch": {"rays_per_fetch": 1}}
+
+
+def pick_fetch(scion, torch, bvh, fn, rays, out, reps=3):
+    """Traversal parameter chosen by measurement (the autotuner's choice for
+    one layout and one kind of ray): the faster fetch mode."""
+    best, best_t = None, None
+    for name, p in FETCH_MODES.items():
+        fn(bvh, rays, out, params=p or None)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn(bvh, rays, out, params=p or None)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        t = min(ts)
+        if best_t is None or t < best_t:
+            best, best_t = name, t
+    return best
+
+
 def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler=None):
     """K timed steps of (primary closest, bounce closest, shadow any); events
-    on the launching stream around each launch."""
+    on the launching stream around each launch. Each kind of ray uses the
+    fetch mode measured fastest for it."""
     d_p, d_b, d_s = rays
     o_p, o_b, o_s = outs
+    fns = (scion.scion_trace_closest, scion.scion_trace_closest, scion.scion_trace_any)
+    modes = [pick_fetch(scion, torch, bvh, f, r, o) for f, r, o in zip(fns, rays, outs)]
+    ps = [FETCH_MODES[m] or None for m in modes]
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        scion.scion_trace_closest(bvh, d_p, o_p)
-        scion.scion_trace_closest(bvh, d_b, o_b)
-        scion.scion_trace_any(bvh, d_s, o_s)
+        scion.scion_trace_closest(bvh, d_p, o_p, params=ps[0])
+        scion.scion_trace_closest(bvh, d_b, o_b, params=ps[1])
+        scion.scion_trace_any(bvh, d_s, o_s, params=ps[2])
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     t_start = time.time()
@@ -186,21 +214,21 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
         flush_l2(flush_buf)
         e = ev[k]
         e[0].record(stream)
-        scion.scion_trace_closest(bvh, d_p, o_p)
+        scion.scion_trace_closest(bvh, d_p, o_p, params=ps[0])
         e[1].record(stream)
-        scion.scion_trace_closest(bvh, d_b, o_b)
+        scion.scion_trace_closest(bvh, d_b, o_b, params=ps[1])
         e[2].record(stream)
-        scion.scion_trace_any(bvh, d_s, o_s)
+        scion.scion_trace_any(bvh, d_s, o_s, params=ps[2])
         e[3].record(stream)
     torch.cuda.synchronize()
     if sampler:
         sampler.window(t_start, time.time())
     per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in ev])  # ms
     step = per.sum(axis=1)
-    return step, per
+    return step, per, modes
 
 
-def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf):
+def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("warp_batch",) * 3):
     """The same step through the public API from pinned host buffers: every
     step copies its rays host->device, traces, and reads the results back."""
     dev = torch.device("cuda")
@@ -213,12 +241,14 @@ def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf):
     d_out = [torch.empty_like(h, device=dev) for h in h_out]
     stream = torch.cuda.current_stream()
 
+    ps = [FETCH_MODES[m] or None for m in modes]
+
     def step():
         for h, d in zip(h_in, d_in):
             d.copy_(h, non_blocking=True)
-        scion.scion_trace_closest(bvh, d_in[0], d_out[0])
-        scion.scion_trace_closest(bvh, d_in[1], d_out[1])
-        scion.scion_trace_any(bvh, d_in[2], d_out[2])
+        scion.scion_trace_closest(bvh, d_in[0], d_out[0], params=ps[0])
+        scion.scion_trace_closest(bvh, d_in[1], d_out[1], params=ps[1])
+        scion.scion_trace_any(bvh, d_in[2], d_out[2], params=ps[2])
         for h, d in zip(h_out, d_out):
             h.copy_(d, non_blocking=True)
 
@@ -348,20 +378,22 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
         res = {}
         for q, fn, r, o in (("closest", scion.scion_trace_closest, rays, hits),
                             ("any", scion.scion_trace_any, short, occ)):
+            mode = pick_fetch(scion, torch, bvh, fn, r, o, reps=2)
+            p = FETCH_MODES[mode] or None
             for _ in range(warmup):
-                fn(bvh, r, o)
+                fn(bvh, r, o, params=p)
             torch.cuda.synchronize()
             ts = []
             for _ in range(steps):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record()
-                fn(bvh, r, o)
+                fn(bvh, r, o, params=p)
                 b.record()
                 b.synchronize()
                 ts.append(a.elapsed_time(b))
             ms = trimmed_mean(ts)
             gbs = alg[q] / (ms / 1e3) / 1e9
-            res[q] = {"ms": ms, "mrays_s": n / (ms / 1e3) / 1e6, "bytes_per_ray": alg[q] / n,
+            res[q] = {"ms": ms, "mrays_s": n / (ms / 1e3) / 1e6, "bytes_per_ray": alg[q] / n, "fetch_mode": mode,
                       "alg_gbs": gbs, "roofline_frac_of_measured_hbm": gbs / hbm_peak}
         res["bvh_mb"] = (info["node_bytes"] + info["prim_bytes"]) / 1e6
         res["nodes_per_ray"] = {"closest": float(cc[0]) / n, "any": float(ca[0]) / n}
@@ -576,7 +608,7 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-        step, per = time_layout(scion, torch, bvh, rays, outs, args.steps, args.warmup, flush_buf, sampler)
+        step, per, modes = time_layout(scion, torch, bvh, rays, outs, args.steps, args.warmup, flush_buf, sampler)
         ms = trimmed_mean(step.tolist())
         if dist is not None:
             t = torch.tensor([ms], device=dev)
@@ -596,6 +628,7 @@ def main():
             "nodes_per_ray": {q: float(cnt[i][0]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
             "tris_per_ray": {q: float(cnt[i][2]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
             "alg_bytes": alg, "device_status": st_status,
+            "fetch_mode": {"primary": modes[0], "bounce": modes[1], "shadow": modes[2]},
         }
         results[name]["_bvh"] = bvh
 
@@ -614,7 +647,9 @@ def main():
                 "note": "algorithmic bytes = rays x 48 + nodes visited x node bytes + triangles tested x "
                         "triangle bytes (counting kernel); this BVH fits in L2, so DRAM traffic is far lower"}
     # end to end through host buffers, best layout
-    e2e_t, bi, bo = e2e_layout(scion, torch, r["_bvh"], (prim, bounce, shadow), args.steps, args.warmup, flush_buf)
+    fm = r["fetch_mode"]
+    e2e_t, bi, bo = e2e_layout(scion, torch, r["_bvh"], (prim, bounce, shadow), args.steps, args.warmup, flush_buf,
+                               (fm["primary"], fm["bounce"], fm["shadow"]))
     e2e_ms = trimmed_mean(e2e_t)
     if dist is not None:
         t = torch.tensor([e2e_ms], device=dev)

@@ -112,7 +112,13 @@ typedef struct {
  *  smem_stack        : shared-memory stack entries per thread (default 16).
  *  ordered_children  : 0 or 1 = visit nearer children first (closest-hit),
  *                      2 = stored slot order.
- *  rays_per_fetch    : reserved (0); each warp fetches 32 rays at a time.
+ *  rays_per_fetch    : 0 (or 32) = each warp takes 32 consecutive rays and
+ *                      traces them to completion; 1 = each lane takes its
+ *                      next ray as soon as it finishes one (32-ray blocks are
+ *                      dealt to the CTAs round-robin, rays handed out from a
+ *                      shared-memory counter). Results are identical; which
+ *                      is faster depends on the layout and the rays.
+ *                      Other values: SCION_ERR_INVALID_ARG.
  *  max_steps         : per-ray node+leaf visit limit (0 = derived from size).
  *  reserved          : must be 0. */
 typedef struct {

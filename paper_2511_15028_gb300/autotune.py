@@ -20,7 +20,12 @@ CANDIDATE_LAYOUTS = {
     "bvh8_soa_f16": dict(width=8, box_layout="soa", box_prec="f16"),
     "bvh8_aos_u8": dict(width=8, box_layout="aos", box_prec="u8"),
 }
+# Traversal parameters the batched launch honours (child order). Plain
+# launches can also choose the fetch mode (per-lane fetch: rays_per_fetch=1).
 CANDIDATE_PARAMS = {"ordered": {}, "slot_order": {"ordered_children": 2}}
+CANDIDATE_PARAMS_PLAIN = {**CANDIDATE_PARAMS,
+                          "ordered_lane_fetch": {"rays_per_fetch": 1},
+                          "slot_order_lane_fetch": {"ordered_children": 2, "rays_per_fetch": 1}}
 
 
 @dataclass

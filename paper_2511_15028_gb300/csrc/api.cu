@@ -207,7 +207,8 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
     return SCION_ERR_INVALID_ARG;
   scion_trace_params p{};
   if (params) p = *params;
-  if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch != 0) return SCION_ERR_INVALID_ARG;
+  if (p.reserved != 0 || p.reg_stack != 0 || (p.rays_per_fetch > 1 && p.rays_per_fetch != 32))
+    return SCION_ERR_INVALID_ARG;
   uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
   uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
@@ -244,6 +245,7 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
   a.ordered = ordered;
   a.smem_stack = smem_entries;
+  a.lane_fetch = p.rays_per_fetch == 1 ? 1u : 0u;
   a.work = reinterpret_cast<unsigned long long *>(b->d_scratch);
   a.exit_count = b->d_scratch + 2;
   a.status = b->d_scratch + 3;
@@ -508,6 +510,7 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
     a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
     a.ordered = p.ordered_children == 2 ? 0u : 1u;
     a.smem_stack = bt->smem_stack;
+    a.lane_fetch = 0;
     a.status = b->d_scratch + 3;
     sc.begin = total;
     sc.family = (uint32_t)fam;
@@ -738,7 +741,8 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
     return SCION_ERR_INVALID_ARG;
   scion_trace_params p{};
   if (params) p = *params;
-  if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch != 0 || p.ordered_children > 2)
+  if (p.reserved != 0 || p.reg_stack != 0 || (p.rays_per_fetch > 1 && p.rays_per_fetch != 32) ||
+      p.ordered_children > 2)
     return SCION_ERR_INVALID_ARG;
   const uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
@@ -780,6 +784,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
   a.ordered = p.ordered_children == 2 ? 0u : 1u;
   a.smem_stack = smem_entries;
+  a.lane_fetch = p.rays_per_fetch == 1 ? 1u : 0u;
   a.work = static_cast<unsigned long long *>(scratch);
   a.exit_count = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(scratch) + 8);
   a.status = b->d_scratch + 3;  // device errors still go to the BVH's status word

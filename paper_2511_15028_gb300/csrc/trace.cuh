@@ -45,6 +45,7 @@ struct TraceArgs {
   uint32_t max_steps;
   uint32_t ordered;
   uint32_t smem_stack;      // shared-memory stack entries per thread
+  uint32_t lane_fetch;      // 0: 32-ray warp batches, 1: per-lane fetch
   unsigned long long *work; // persistent work counter (self-resetting)
   uint32_t *exit_count;     // CTAs finished (self-resetting)
   uint32_t *status;         // first device error code
@@ -516,13 +517,7 @@ __device__ __forceinline__ void trace_lane(const TraceArgs &a, Lane &L, Stack &s
 // Persistent warps: each warp takes 32 consecutive rays with one atomicAdd on
 // the global counter, every lane traces one of them to completion, repeat.
 template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
-  extern __shared__ uint2 smem_stack[];
-  Stack st;
-  st.sh = smem_stack + threadIdx.x;
-  st.stride = blockDim.x;
-  st.cap_sh = (int)a.smem_stack;
-  st.sp = 0;
+__device__ __forceinline__ void body_warp_batch(const TraceArgs &a, Stack &st) {
   Counts cnt;
   uint32_t n_rays = 0;
   const uint32_t lane = threadIdx.x & 31u;
@@ -571,6 +566,82 @@ __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
       __threadfence();
     }
   }
+}
+
+// Per-lane ray fetch. The rays are cut into 32-ray
+// blocks dealt to the CTAs round-robin (CTA c owns blocks c, c + G, c + 2G,
+// ... for a grid of G CTAs), so every CTA sees a spatially uniform share and
+// no global atomic is needed. Inside a CTA a shared counter hands out the
+// CTA's rays one at a time: a lane takes its next ray the moment it finishes
+// the previous one, so a warp never idles on its slowest ray.
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
+__device__ __forceinline__ void body_lane_fetch(const TraceArgs &a, Stack &st) {
+  __shared__ uint32_t cta_next;
+  if (threadIdx.x == 0) cta_next = 0;
+  __syncthreads();
+  Counts cnt;
+  uint32_t n_rays = 0;
+  const unsigned long long G = gridDim.x, c = blockIdx.x;
+  Lane L;
+  L.cur = kEmptyRef;
+  bool has_ray = false;
+  while (true) {
+    if (!has_ray) {
+      const uint32_t j = atomicAdd(&cta_next, 1u);
+      const unsigned long long rid = (c + (unsigned long long)(j >> 5) * G) * 32ull + (j & 31u);
+      if (rid >= a.n) break;
+      L.rid = rid;
+      setup_ray(ldg4f(a.rays + 2 * rid), ldg4f(a.rays + 2 * rid + 1), L.r);
+      L.b = Best{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_MISS};
+      L.steps = 0;
+      L.err = 0;
+      L.found = false;
+      st.sp = 0;
+      if constexpr (OWN) L.cur = a.n_nodes > 0 ? 0u : kEmptyRef;
+      else L.cur = a.root_ref;
+      has_ray = true;
+      if (STATS) n_rays++;
+    }
+    if (L.cur != kEmptyRef) {
+      if (++L.steps > a.max_steps) {
+        L.err = kErrIter;
+        L.cur = kEmptyRef;
+      } else {
+        if constexpr (OWN) step_bin<SOA, CREF, ANY, STATS>(a, L, st, cnt);
+        else step_wide<W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
+      }
+    }
+    if (L.cur == kEmptyRef) {
+      if (L.err) atomicCAS(a.status, 0u, L.err);
+      if (ANY) {
+        static_cast<uint32_t *>(a.out)[L.rid] = L.err ? SCION_PRIM_ERROR : (L.found ? 1u : 0u);
+      } else {
+        if (L.err) L.b = Best{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_ERROR};
+        static_cast<uint4 *>(a.out)[L.rid] =
+            make_uint4(__float_as_uint(L.b.t), __float_as_uint(L.b.u), __float_as_uint(L.b.v), L.b.id);
+      }
+      has_ray = false;
+    }
+  }
+  if (STATS) {
+    atomicAdd(a.stats + 0, (unsigned long long)cnt.nodes);
+    atomicAdd(a.stats + 1, (unsigned long long)cnt.leaves);
+    atomicAdd(a.stats + 2, (unsigned long long)cnt.prims);
+    atomicAdd(a.stats + 3, (unsigned long long)n_rays);
+  }
+}
+
+
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
+__device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
+  extern __shared__ uint2 smem_stack[];
+  Stack st;
+  st.sh = smem_stack + threadIdx.x;
+  st.stride = blockDim.x;
+  st.cap_sh = (int)a.smem_stack;
+  st.sp = 0;
+  if (a.lane_fetch) body_lane_fetch<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, st);
+  else body_warp_batch<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, st);
 }
 
 }  // namespace scion

@@ -72,6 +72,9 @@ def test_config1_every_layout_bit_exact(sc_mod, config1, kw):
     assert np.array_equal(gpu_any(sc_mod, bvh, rays), occ)
     unordered = gpu_closest(sc_mod, bvh, rays, params=dict(ordered_children=2))
     assert_same_hits(unordered, exp, "unordered")
+    lane = gpu_closest(sc_mod, bvh, rays, params=dict(rays_per_fetch=1))
+    assert_same_hits(lane, exp, "per-lane fetch")
+    assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(rays_per_fetch=1)), occ)
     assert sc_mod.scion_get_status(bvh) == 0
 
 
@@ -218,5 +221,6 @@ def test_random_soup_incoherent(sc_mod, oracle_mod):
     eocc = ob.any(short)
     for name, d in sc_mod.sweep_layouts().items():
         bvh = sc_mod.scion_build(verts, d)
-        assert_same_hits(gpu_closest(sc_mod, bvh, rays), exp, name)
-        assert np.array_equal(gpu_any(sc_mod, bvh, short), eocc), name
+        for p in (None, dict(rays_per_fetch=1), dict(rays_per_fetch=1, ordered_children=2, threads_per_block=128)):
+            assert_same_hits(gpu_closest(sc_mod, bvh, rays, params=p), exp, name + " " + str(p))
+            assert np.array_equal(gpu_any(sc_mod, bvh, short, params=p), eocc), name + " " + str(p)
