@@ -229,38 +229,29 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
 
 
 def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("warp_batch",) * 3):
-    """The same step through the public API from pinned host buffers: every
-    step copies its rays host->device, traces, and reads the results back."""
-    dev = torch.device("cuda")
+    """The same step through the public API from pinned host memory: every
+    step copies its rays host->device and its results device->host, pipelined
+    in chunks on three streams (scion.HostTracer) so that the copies overlap
+    the traversal."""
     h_in = [torch.from_numpy(r).pin_memory() for r in host_rays]
-    d_in = [torch.empty_like(h, device=dev) for h in h_in]
     n = [r.shape[0] for r in host_rays]
     h_out = [torch.empty((n[0], 4), dtype=torch.int32).pin_memory(),
              torch.empty((n[1], 4), dtype=torch.int32).pin_memory(),
              torch.empty((n[2],), dtype=torch.int32).pin_memory()]
-    d_out = [torch.empty_like(h, device=dev) for h in h_out]
-    stream = torch.cuda.current_stream()
-
     ps = [FETCH_MODES[m] or None for m in modes]
-
-    def step():
-        for h, d in zip(h_in, d_in):
-            d.copy_(h, non_blocking=True)
-        scion.scion_trace_closest(bvh, d_in[0], d_out[0], params=ps[0])
-        scion.scion_trace_closest(bvh, d_in[1], d_out[1], params=ps[1])
-        scion.scion_trace_any(bvh, d_in[2], d_out[2], params=ps[2])
-        for h, d in zip(h_out, d_out):
-            h.copy_(d, non_blocking=True)
-
+    jobs = [(bvh, h_in[0], h_out[0], "closest", ps[0]), (bvh, h_in[1], h_out[1], "closest", ps[1]),
+            (bvh, h_in[2], h_out[2], "any", ps[2])]
+    tracer = scion.HostTracer()
+    stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        step()
+        tracer.trace(jobs)
     torch.cuda.synchronize()
     times = []
     for _ in range(steps):
         flush_l2(flush_buf)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step()
+        tracer.trace(jobs)
         b.record(stream)
         b.synchronize()
         times.append(a.elapsed_time(b))

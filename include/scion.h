@@ -19,9 +19,9 @@
  *    prim = SCION_PRIM_ERROR; scion_get_status reads and clears that word.
  *  - Device pointers are CUDA device addresses on the current device.
  *  - Rays and hits are caller-owned. The BVH owns its own device buffers.
- *  - One BVH may be traced by several calls in a row on one stream. Calls on
- *    the same BVH issued concurrently on different streams share its device
- *    work counter and race: order them on one stream.
+ *  - One BVH may be traced concurrently from up to 64 distinct streams: each
+ *    stream gets its own work counter in the BVH (calls on one stream run in
+ *    order). A 65th stream is refused with SCION_ERR_INVALID_ARG.
  */
 #ifndef SCION_H
 #define SCION_H

@@ -18,6 +18,10 @@
 
 using namespace scion;
 
+namespace {
+constexpr uint32_t kStreamSlotCount = 64;  // distinct streams one BVH can be traced on
+}
+
 struct scion_bvh_s {
   scion_layout_desc desc;
   bool own_box = false;
@@ -28,7 +32,13 @@ struct scion_bvh_s {
   uint64_t node_bytes = 0, node2_bytes = 0, prim_bytes = 0, idx_bytes = 0, vert_bytes = 0;
   void *d_nodes = nullptr, *d_nodes2 = nullptr, *d_prims = nullptr, *d_prim_ids = nullptr;
   void *d_verts = nullptr, *d_idx = nullptr;
-  uint32_t *d_scratch = nullptr;  // u64 work counter, u32 exit counter, u32 status
+  // device scratch: words 0-3 hold the status word (word 3); then one 16-byte
+  // slot per stream that has traced this BVH (u64 work counter, u32 exit
+  // counter, pad), so launches on different streams never share a counter
+  uint32_t *d_scratch = nullptr;
+  std::mutex slot_mu;
+  uint32_t n_slots = 0;
+  cudaStream_t slot_stream[kStreamSlotCount] = {};
   double build_ms = 0.0;
   int device = 0;
 };
@@ -36,6 +46,18 @@ struct scion_bvh_s {
 namespace {
 
 std::string g_last_error;
+constexpr size_t kScratchBytes = 16 + 16 * kStreamSlotCount;
+
+// Counter slot of `stream` for this BVH (assigned on first use), or -1 when
+// kStreamSlotCount other streams already hold slots.
+int stream_slot(scion_bvh b, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(b->slot_mu);
+  for (uint32_t i = 0; i < b->n_slots; ++i)
+    if (b->slot_stream[i] == stream) return (int)i;
+  if (b->n_slots == kStreamSlotCount) return -1;
+  b->slot_stream[b->n_slots] = stream;
+  return (int)b->n_slots++;
+}
 
 scion_status cuda_fail(cudaError_t e) {
   g_last_error = cudaGetErrorString(e);
@@ -246,8 +268,14 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   a.ordered = ordered;
   a.smem_stack = smem_entries;
   a.lane_fetch = p.rays_per_fetch == 1 ? 1u : 0u;
-  a.work = reinterpret_cast<unsigned long long *>(b->d_scratch);
-  a.exit_count = b->d_scratch + 2;
+  const int slot = stream_slot(b, stream);
+  if (slot < 0) {
+    g_last_error = "more than 64 streams have traced this BVH";
+    return SCION_ERR_INVALID_ARG;
+  }
+  uint32_t *sl = b->d_scratch + 4 + 4 * slot;
+  a.work = reinterpret_cast<unsigned long long *>(sl);
+  a.exit_count = sl + 2;
   a.status = b->d_scratch + 3;
   a.stats = stats;
   void *args[] = {&a};
@@ -284,8 +312,8 @@ scion_status upload_bvh(HostBVH &hb, uint64_t n_tris, uint64_t n_verts, bool ind
   if (us == SCION_OK) us = upload(&b->d_verts, hb.verts4, s, &b->vert_bytes);
   if (us == SCION_OK) us = upload(&b->d_idx, hb.indices, s, &b->idx_bytes);
   if (us == SCION_OK) {
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_scratch), 4 * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scratch, 0, 4 * sizeof(uint32_t), s);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_scratch), kScratchBytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scratch, 0, kScratchBytes, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) us = e == cudaErrorMemoryAllocation ? SCION_ERR_OOM : cuda_fail(e);
   }

@@ -400,6 +400,73 @@ def scion_trace_batched(bvhs, rays, hits=None, params=None, stream=None):
     return b.hits
 
 
+class HostTracer:
+    """Traces rays that live in pinned host memory and returns the results
+    to pinned host memory, overlapping transfers with traversal: each ray set
+    is cut into chunks, and chunk i's host-to-device copy, trace and
+    device-to-host copy run on stream i mod n_streams, so the copies of one
+    chunk overlap the traversal of the others. Device staging buffers are
+    allocated once (on first use) and reused."""
+
+    def __init__(self, n_streams: int = 3, chunk_rays: int = 1 << 19):
+        import torch
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.chunk = chunk_rays
+        self._rays = [None] * n_streams
+        self._outs = [None] * n_streams
+
+    def _buf(self, i, n_rows, width, dtype, which):
+        import torch
+        cache = self._rays if which == "rays" else self._outs
+        b = cache[i]
+        if b is None or b.shape[0] < n_rows or b.shape[1:] != width or b.dtype != dtype:
+            shape = (max(n_rows, self.chunk),) + width
+            b = torch.empty(shape, dtype=dtype, device="cuda")
+            cache[i] = b
+        return b[:n_rows]
+
+    def trace(self, jobs):
+        """jobs: list of (bvh, host_rays [n, 8] float32 pinned, host_out
+        pinned (int32 [n, 4] for closest, int32 [n] for any), query
+        ('closest' | 'any'), params or None). Issues everything and makes the
+        current stream wait for it: the host outputs are complete once the
+        current stream reaches this point (e.g. after an event on it)."""
+        import torch
+        cur = torch.cuda.current_stream()
+        for s in self.streams:
+            s.wait_stream(cur)
+        k = 0
+        for bvh, h_rays, h_out, query, params in jobs:
+            n = h_rays.shape[0]
+            for b in range(0, n, self.chunk):
+                e = min(n, b + self.chunk)
+                i = k % len(self.streams)
+                s = self.streams[i]
+                with torch.cuda.stream(s):
+                    d_r = self._buf(i, e - b, (8,), torch.float32, "rays")
+                    d_r.copy_(h_rays[b:e], non_blocking=True)
+                    if query == "closest":
+                        d_o = self._buf(i, e - b, (4,), torch.int32, "outs")
+                        scion_trace_closest(bvh, d_r, d_o, params=params, stream=s)
+                    else:
+                        d_o = self._any_buf(i, e - b)
+                        scion_trace_any(bvh, d_r, d_o, params=params, stream=s)
+                    h_out[b:e].copy_(d_o, non_blocking=True)
+                k += 1
+        for s in self.streams:
+            cur.wait_stream(s)
+
+    def _any_buf(self, i, n):
+        import torch
+        if not hasattr(self, "_anys"):
+            self._anys = [None] * len(self.streams)
+        b = self._anys[i]
+        if b is None or b.shape[0] < n:
+            b = torch.empty((max(n, self.chunk),), dtype=torch.int32, device="cuda")
+            self._anys[i] = b
+        return b[:n]
+
+
 def scion_get_status(bvh: BVH, stream=None) -> int:
     st = ctypes.c_int()
     _check(lib().scion_get_status(bvh.handle, _stream_ptr(stream), ctypes.byref(st)), "scion_get_status")

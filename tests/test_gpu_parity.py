@@ -224,3 +224,42 @@ def test_random_soup_incoherent(sc_mod, oracle_mod):
         for p in (None, dict(rays_per_fetch=1), dict(rays_per_fetch=1, ordered_children=2, threads_per_block=128)):
             assert_same_hits(gpu_closest(sc_mod, bvh, rays, params=p), exp, name + " " + str(p))
             assert np.array_equal(gpu_any(sc_mod, bvh, short, params=p), eocc), name + " " + str(p)
+
+
+def test_concurrent_streams_same_bvh_and_host_tracer(sc_mod, oracle_mod):
+    """Traces of one BVH issued on several streams at once (each stream has its
+    own work counter) and the pipelined host-buffer tracer give the oracle's
+    results."""
+    rng = scenes.rng_for(41)
+    verts = scenes.random_soup(rng, 1 << 16, mu=np.log(0.01))
+    tris = verts.reshape(-1, 9)
+    rays = scenes.random_rays(rng, 200_000, (0, 0, 0), (1, 1, 1))
+    short = rays.copy()
+    short[:, 7] = 0.05
+    ob = oracle_mod.BVH2(tris)
+    exp, eocc = ob.closest(rays), ob.any(short)
+    bvh = sc_mod.scion_build(verts, sc_mod.layout(width=4, box_layout="soa", prim_ref="direct"))
+    d = torch.from_numpy(rays).cuda()
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    outs = [torch.empty((rays.shape[0], 4), dtype=torch.int32, device="cuda") for _ in streams]
+    for _ in range(3):
+        for st, o in zip(streams, outs):
+            o.fill_(0)
+            st.wait_stream(torch.cuda.current_stream())
+            sc_mod.scion_trace_closest(bvh, d, o, stream=st)
+        torch.cuda.synchronize()
+        for o in outs:
+            assert_same_hits(sc_mod.split_hits(o), exp, "concurrent")
+    h_r = torch.from_numpy(rays).pin_memory()
+    h_s = torch.from_numpy(short).pin_memory()
+    h_o = torch.empty((rays.shape[0], 4), dtype=torch.int32).pin_memory()
+    h_a = torch.empty((rays.shape[0],), dtype=torch.int32).pin_memory()
+    tracer = sc_mod.HostTracer(n_streams=3, chunk_rays=30_000)
+    for p in (None, dict(rays_per_fetch=1)):
+        h_o.fill_(0)
+        h_a.fill_(7)
+        tracer.trace([(bvh, h_r, h_o, "closest", p), (bvh, h_s, h_a, "any", p)])
+        torch.cuda.synchronize()
+        assert_same_hits(sc_mod.split_hits(h_o), exp, f"host tracer {p}")
+        assert np.array_equal(h_a.numpy().astype(np.uint32), eocc)
+    assert sc_mod.scion_get_status(bvh) == 0
