@@ -169,14 +169,20 @@ def flush_l2(buf):
     buf.zero_()
 
 
-FETCH_MODES = {"warp_batch": {}, "lane_fetch": {"rays_per_fetch": 1}}
+# Traversal parameters tried per layout and kind of ray (fetch mode x child
+# order); any-hit ignores the child order.
+FETCH_MODES = {"warp_batch": {}, "lane_fetch": {"rays_per_fetch": 1},
+               "warp_batch/nearest_first": {"ordered_children": 3},
+               "lane_fetch/nearest_first": {"rays_per_fetch": 1, "ordered_children": 3}}
 
 
 def pick_fetch(scion, torch, bvh, fn, rays, out, reps=3):
-    """Traversal parameter chosen by measurement (the autotuner's choice for
-    one layout and one kind of ray): the faster fetch mode."""
+    """Traversal parameters chosen by measurement (the autotuner's choice for
+    one layout and one kind of ray): the fastest candidate."""
     best, best_t = None, None
-    for name, p in FETCH_MODES.items():
+    cands = FETCH_MODES if fn is scion.scion_trace_closest else {
+        k: v for k, v in FETCH_MODES.items() if "nearest" not in k}
+    for name, p in cands.items():
         fn(bvh, rays, out, params=p or None)
         torch.cuda.synchronize()
         ts = []

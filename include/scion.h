@@ -110,8 +110,9 @@ typedef struct {
  *  ctas_per_sm       : persistent CTAs per SM (default: from occupancy).
  *  reg_stack         : reserved (0).
  *  smem_stack        : shared-memory stack entries per thread (default 16).
- *  ordered_children  : 0 or 1 = visit nearer children first (closest-hit),
- *                      2 = stored slot order.
+ *  ordered_children  : 0 or 1 = children sorted by entry distance
+ *                      (closest hit), 2 = stored slot order, 3 = nearest
+ *                      child first and the others in slot order.
  *  rays_per_fetch    : 0 (or 32) = each warp takes 32 consecutive rays and
  *                      traces them to completion; 1 = each lane takes its
  *                      next ray as soon as it finishes one (32-ray blocks are

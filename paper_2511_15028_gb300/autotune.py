@@ -22,10 +22,12 @@ CANDIDATE_LAYOUTS = {
 }
 # Traversal parameters the batched launch honours (child order). Plain
 # launches can also choose the fetch mode (per-lane fetch: rays_per_fetch=1).
-CANDIDATE_PARAMS = {"ordered": {}, "slot_order": {"ordered_children": 2}}
+CANDIDATE_PARAMS = {"ordered": {}, "slot_order": {"ordered_children": 2},
+                    "nearest_first": {"ordered_children": 3}}
 CANDIDATE_PARAMS_PLAIN = {**CANDIDATE_PARAMS,
                           "ordered_lane_fetch": {"rays_per_fetch": 1},
-                          "slot_order_lane_fetch": {"ordered_children": 2, "rays_per_fetch": 1}}
+                          "slot_order_lane_fetch": {"ordered_children": 2, "rays_per_fetch": 1},
+                          "nearest_first_lane_fetch": {"ordered_children": 3, "rays_per_fetch": 1}}
 
 
 @dataclass

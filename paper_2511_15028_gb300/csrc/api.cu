@@ -48,6 +48,9 @@ namespace {
 std::string g_last_error;
 constexpr size_t kScratchBytes = 16 + 16 * kStreamSlotCount;
 
+// scion_trace_params.ordered_children -> kernel order mode
+uint32_t order_mode(uint32_t oc) { return oc == 2 ? 0u : (oc == 3 ? 2u : 1u); }
+
 // Counter slot of `stream` for this BVH (assigned on first use), or -1 when
 // kStreamSlotCount other streams already hold slots.
 int stream_slot(scion_bvh b, cudaStream_t stream) {
@@ -235,8 +238,8 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
   uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
   if (smem_entries > 64) return SCION_ERR_INVALID_ARG;
-  if (p.ordered_children > 2) return SCION_ERR_INVALID_ARG;
-  const uint32_t ordered = p.ordered_children == 2 ? 0u : 1u;
+  if (p.ordered_children > 3) return SCION_ERR_INVALID_ARG;
+  const uint32_t ordered = order_mode(p.ordered_children);
   TraceKernel k = pick_kernel(b, any, stats ? 1 : 0);
   if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
   const size_t smem = (size_t)tpb * smem_entries * sizeof(uint2);
@@ -506,7 +509,7 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
     scion_bvh b = bvhs[i];
     scion_trace_params p{};
     if (per_scene) p = per_scene[i];
-    if (!b || (n[i] > 0 && (!d_rays[i] || !d_hits[i])) || p.ordered_children > 2 ||
+    if (!b || (n[i] > 0 && (!d_rays[i] || !d_hits[i])) || p.ordered_children > 3 ||
         (reinterpret_cast<uintptr_t>(d_rays[i]) & 15u) || (reinterpret_cast<uintptr_t>(d_hits[i]) & 15u)) {
       delete bt;
       return SCION_ERR_INVALID_ARG;
@@ -536,7 +539,7 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
     a.n_nodes = b->n_nodes;
     a.prim_indirect = b->desc.prim_ref;
     a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
-    a.ordered = p.ordered_children == 2 ? 0u : 1u;
+    a.ordered = order_mode(p.ordered_children);
     a.smem_stack = bt->smem_stack;
     a.lane_fetch = 0;
     a.status = b->d_scratch + 3;
@@ -770,7 +773,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   scion_trace_params p{};
   if (params) p = *params;
   if (p.reserved != 0 || p.reg_stack != 0 || (p.rays_per_fetch > 1 && p.rays_per_fetch != 32) ||
-      p.ordered_children > 2)
+      p.ordered_children > 3)
     return SCION_ERR_INVALID_ARG;
   const uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
@@ -810,7 +813,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   a.n_nodes = b->n_nodes;
   a.prim_indirect = b->desc.prim_ref;
   a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
-  a.ordered = p.ordered_children == 2 ? 0u : 1u;
+  a.ordered = order_mode(p.ordered_children);
   a.smem_stack = smem_entries;
   a.lane_fetch = p.rays_per_fetch == 1 ? 1u : 0u;
   a.work = static_cast<unsigned long long *>(scratch);

@@ -43,7 +43,7 @@ struct TraceArgs {
   uint32_t n_nodes;
   uint32_t prim_indirect;
   uint32_t max_steps;
-  uint32_t ordered;
+  uint32_t ordered;         // 0 slot order, 1 sorted by entry distance, 2 nearest first
   uint32_t smem_stack;      // shared-memory stack entries per thread
   uint32_t lane_fetch;      // 0: 32-ray warp batches, 1: per-lane fetch
   unsigned long long *work; // persistent work counter (self-resetting)
@@ -429,7 +429,14 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
       cref[k] = hit ? ref : kEmptyRef;
       ctn[k] = hit ? tn : __int_as_float(0x7f800000);
     }
-    if (!ANY && a.ordered) sort_children<W>(ctn, cref);
+    if (!ANY && a.ordered == 1) {
+      sort_children<W>(ctn, cref);
+    } else if (!ANY && a.ordered == 2) {
+      // nearest first, the rest in slot order: move the nearest hit child
+      // into slot 0 (one pass of compare-exchanges toward the front)
+#pragma unroll
+      for (int k = W - 1; k > 0; --k) cmpx(ctn, cref, k - 1, k);
+    }
     // push every hit child but the first, last one first; go on with the first
     uint32_t next = kEmptyRef;
     float next_tn = 0.f;

@@ -74,6 +74,8 @@ def test_config1_every_layout_bit_exact(sc_mod, config1, kw):
     assert_same_hits(unordered, exp, "unordered")
     lane = gpu_closest(sc_mod, bvh, rays, params=dict(rays_per_fetch=1))
     assert_same_hits(lane, exp, "per-lane fetch")
+    nearest = gpu_closest(sc_mod, bvh, rays, params=dict(ordered_children=3))
+    assert_same_hits(nearest, exp, "nearest first")
     assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(rays_per_fetch=1)), occ)
     assert sc_mod.scion_get_status(bvh) == 0
 
@@ -221,7 +223,8 @@ def test_random_soup_incoherent(sc_mod, oracle_mod):
     eocc = ob.any(short)
     for name, d in sc_mod.sweep_layouts().items():
         bvh = sc_mod.scion_build(verts, d)
-        for p in (None, dict(rays_per_fetch=1), dict(rays_per_fetch=1, ordered_children=2, threads_per_block=128)):
+        for p in (None, dict(rays_per_fetch=1), dict(rays_per_fetch=1, ordered_children=2, threads_per_block=128),
+                  dict(ordered_children=3), dict(rays_per_fetch=1, ordered_children=3)):
             assert_same_hits(gpu_closest(sc_mod, bvh, rays, params=p), exp, name + " " + str(p))
             assert np.array_equal(gpu_any(sc_mod, bvh, short, params=p), eocc), name + " " + str(p)
 
