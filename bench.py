@@ -5,8 +5,10 @@ Workload (one step): the coherent + incoherent scene of 1,373,138 triangles
 (724 x 724 fBm height field + 256 icospheres), 1920 x 1080 primary camera rays
 (closest hit), one cosine-weighted diffuse bounce ray per primary hit (closest
 hit) and one shadow ray per primary hit toward a point light (any hit), all
-inputs resident in HBM. Every one of the eight swept layouts is timed; the
-headline value is the best layout's whole-step Mrays/s.
+inputs resident in HBM. Every swept layout is timed (the eight layouts of
+the four node families with direct and indirect triangles, and the quantised
+bvh2 layouts sg-pbrt-q16, -soaos, sg-eq and sg-eq-align16); the headline
+value is the best layout's whole-step Mrays/s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -49,6 +51,10 @@ def node_load_bytes(desc) -> int:
     w, prec, cref = desc.width, desc.box_prec, desc.child_ref
     if w == 2 and prec == 0:
         return 32
+    if prec == 3:  # q16 own-box node: 12 B of codes + 4 B word
+        return 16
+    if prec == 4:  # eq10 own-box node: 12 B (16 B aligned)
+        return 16 if desc.align == 16 else 12
     elem = {0: 4, 1: 2, 2: 1}[prec]
     used = (16 if prec == 2 else 0) + w * 6 * elem + (4 * w if cref == 0 else 8 + w)
     return (used + 15) // 16 * 16
@@ -171,15 +177,18 @@ def flush_l2(buf):
 
 # Traversal parameters tried per layout and kind of ray (fetch mode x child
 # order); any-hit ignores the child order.
-FETCH_MODES = {"warp_batch": {}, "lane_fetch": {"rays_per_fetch": 1},
+FETCH_MODES = {"warp_batch": {}, "refill1": {"rays_per_fetch": 1}, "refill8": {"rays_per_fetch": 8},
+               "refill16": {"rays_per_fetch": 16},
                "warp_batch/nearest_first": {"ordered_children": 3},
-               "lane_fetch/nearest_first": {"rays_per_fetch": 1, "ordered_children": 3}}
+               "refill1/nearest_first": {"rays_per_fetch": 1, "ordered_children": 3},
+               "refill8/nearest_first": {"rays_per_fetch": 8, "ordered_children": 3}}
 
 
 def pick_fetch(scion, torch, bvh, fn, rays, out, reps=3):
     """Traversal parameters chosen by measurement (the autotuner's choice for
-    one layout and one kind of ray): the fastest candidate."""
-    best, best_t = None, None
+    one layout and one kind of ray): the fastest candidate, and every
+    candidate's best time in ms."""
+    best, best_t, trials = None, None, {}
     cands = FETCH_MODES if fn is scion.scion_trace_closest else {
         k: v for k, v in FETCH_MODES.items() if "nearest" not in k}
     for name, p in cands.items():
@@ -194,9 +203,10 @@ def pick_fetch(scion, torch, bvh, fn, rays, out, reps=3):
             b.synchronize()
             ts.append(a.elapsed_time(b))
         t = min(ts)
+        trials[name] = round(t, 4)
         if best_t is None or t < best_t:
             best, best_t = name, t
-    return best
+    return best, trials
 
 
 def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler=None):
@@ -206,7 +216,8 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
     d_p, d_b, d_s = rays
     o_p, o_b, o_s = outs
     fns = (scion.scion_trace_closest, scion.scion_trace_closest, scion.scion_trace_any)
-    modes = [pick_fetch(scion, torch, bvh, f, r, o) for f, r, o in zip(fns, rays, outs)]
+    picks = [pick_fetch(scion, torch, bvh, f, r, o) for f, r, o in zip(fns, rays, outs)]
+    modes = [m for m, _ in picks]
     ps = [FETCH_MODES[m] or None for m in modes]
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -231,7 +242,7 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
         sampler.window(t_start, time.time())
     per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in ev])  # ms
     step = per.sum(axis=1)
-    return step, per, modes
+    return step, per, modes, [t for _, t in picks]
 
 
 def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("warp_batch",) * 3):
@@ -354,7 +365,7 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
     short = rays.clone()
     short[:, 7] = 0.05
     gen_s = time.time() - t0
-    lays = scion.sweep_layouts()
+    lays = scion.sweep_layouts(quantised_bvh2=True)
     if only:
         lays = {k: v for k, v in lays.items() if k in only}
     t0 = time.time()
@@ -375,7 +386,7 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
         res = {}
         for q, fn, r, o in (("closest", scion.scion_trace_closest, rays, hits),
                             ("any", scion.scion_trace_any, short, occ)):
-            mode = pick_fetch(scion, torch, bvh, fn, r, o, reps=2)
+            mode, trials = pick_fetch(scion, torch, bvh, fn, r, o, reps=2)
             p = FETCH_MODES[mode] or None
             for _ in range(warmup):
                 fn(bvh, r, o, params=p)
@@ -391,6 +402,7 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
             ms = trimmed_mean(ts)
             gbs = alg[q] / (ms / 1e3) / 1e9
             res[q] = {"ms": ms, "mrays_s": n / (ms / 1e3) / 1e6, "bytes_per_ray": alg[q] / n, "fetch_mode": mode,
+                      "fetch_trials_ms": trials,
                       "alg_gbs": gbs, "roofline_frac_of_measured_hbm": gbs / hbm_peak}
         res["bvh_mb"] = (info["node_bytes"] + info["prim_bytes"]) / 1e6
         res["nodes_per_ray"] = {"closest": float(cc[0]) / n, "any": float(ca[0]) / n}
@@ -398,7 +410,7 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
         out[name] = res
         scion.scion_destroy(bvh)
     best = max(out, key=lambda k: out[k]["closest"]["mrays_s"])
-    return {"tris": sc.n_tris, "rays": n, "gen_s": round(gen_s, 1), "build_8_layouts_s": round(build_s, 1),
+    return {"tris": sc.n_tris, "rays": n, "gen_s": round(gen_s, 1), "build_layouts_s": round(build_s, 1),
             "layouts": out, "best_closest": best,
             "pareto_closest": pareto({k: (v["bvh_mb"], v["closest"]["mrays_s"]) for k, v in out.items()}),
             "pareto_any": pareto({k: (v["bvh_mb"], v["any"]["mrays_s"]) for k, v in out.items()})}
@@ -565,7 +577,7 @@ def main():
             print(json.dumps({"section": "incoherent", "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
         return
 
-    layouts = scion.sweep_layouts()
+    layouts = scion.sweep_layouts(quantised_bvh2=True)
     if args.layouts != "all":
         keep = args.layouts.split(",")
         layouts = {k: v for k, v in layouts.items() if k in keep}
@@ -605,7 +617,8 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-        step, per, modes = time_layout(scion, torch, bvh, rays, outs, args.steps, args.warmup, flush_buf, sampler)
+        step, per, modes, trials = time_layout(scion, torch, bvh, rays, outs, args.steps, args.warmup, flush_buf,
+                                               sampler)
         ms = trimmed_mean(step.tolist())
         if dist is not None:
             t = torch.tensor([ms], device=dev)
@@ -626,6 +639,7 @@ def main():
             "tris_per_ray": {q: float(cnt[i][2]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
             "alg_bytes": alg, "device_status": st_status,
             "fetch_mode": {"primary": modes[0], "bounce": modes[1], "shadow": modes[2]},
+            "fetch_trials_ms": dict(zip(("primary", "bounce", "shadow"), trials)),
         }
         results[name]["_bvh"] = bvh
 

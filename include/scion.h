@@ -63,6 +63,14 @@ typedef enum {
  *  box_prec   : 0 f32, 1 f16 (world frame, rounded outward),
  *               2 u8 (relative to the parent's merged box, rounded outward,
  *               App. D.2 reading). f16/u8 need a children-in-parent node.
+ *               3 q16 and 4 eq10: width-2 own-box nodes whose box is stored
+ *               as integer codes on one grid over the root box ("sg-pbrt-q16"
+ *               of Section 9.2.5 / App. D.3: 16-bit codes, 16 B per node;
+ *               "sg-eq" of App. D.1: 10-bit codes, 12 B per node). Codes are
+ *               chosen so that the decoded box encloses the node's box.
+ *               These need leaf_max <= 15 and fewer than 2^26 nodes; q16
+ *               takes AoS or SoA ("-soaos": code array + word array), eq10
+ *               AoS only.
  *  child_ref  : 0 direct (an explicit reference per child; for the width-2
  *               own-box node: implicit left = I+1 and stored right offset,
  *               which requires order = DFS), 1 indirect (one base index,
@@ -75,7 +83,11 @@ typedef enum {
  *  leaf_max   : triangles per leaf, 1..16 (0 = 4).
  *  sah_bins   : SAH bins, 2..64 (0 = 16).
  *  treelet_bytes : treelet budget in bytes (0 = 1024).
- *  reserved   : must be 0.
+ *  align      : 0 or 16. 16 pads each own-box node record (or SoA box
+ *               record) to a multiple of 16 bytes ("-align16" of Table 1:
+ *               eq10 12 -> 16 B, q16 SoA codes 12 -> 16 B, f32 SoA boxes
+ *               24 -> 32 B); layouts already 16-byte multiples are unchanged.
+ *               Other values: SCION_ERR_INVALID_ARG.
  * Unsupported combinations return SCION_ERR_UNSUPPORTED_LAYOUT. */
 typedef struct {
   uint32_t width;
@@ -87,7 +99,7 @@ typedef struct {
   uint32_t leaf_max;
   uint32_t sah_bins;
   uint32_t treelet_bytes;
-  uint32_t reserved;
+  uint32_t align;
 } scion_layout_desc;
 
 /* A ray (the paper's Ray of Fig. 4 with an added tmin): accepted hits satisfy
@@ -114,12 +126,13 @@ typedef struct {
  *                      (closest hit), 2 = stored slot order, 3 = nearest
  *                      child first and the others in slot order.
  *  rays_per_fetch    : 0 (or 32) = each warp takes 32 consecutive rays and
- *                      traces them to completion; 1 = each lane takes its
- *                      next ray as soon as it finishes one (32-ray blocks are
- *                      dealt to the CTAs round-robin, rays handed out from a
- *                      shared-memory counter). Results are identical; which
- *                      is faster depends on the layout and the rays.
- *                      Other values: SCION_ERR_INVALID_ARG.
+ *                      traces them to completion; k in 1..31 = a warp
+ *                      refills its idle lanes as soon as at least k of them
+ *                      are idle (32-ray blocks are dealt to the CTAs
+ *                      round-robin, rays handed out from a shared-memory
+ *                      counter; k = 1 refills a lane at the next step).
+ *                      Results are identical; which is faster depends on the
+ *                      layout and the rays. Above 32: SCION_ERR_INVALID_ARG.
  *  max_steps         : per-ray node+leaf visit limit (0 = derived from size).
  *  reserved          : must be 0. */
 typedef struct {

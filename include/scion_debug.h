@@ -32,7 +32,7 @@ typedef struct {
   uint32_t depth;          /* levels of the stored tree */
   uint32_t stack_need;     /* worst-case traversal stack entries */
   uint32_t own_box;        /* 1 = width-2 own-box node */
-  uint32_t reserved;
+  uint32_t node2_bytes;    /* second node array (own-box SoA words/refs), bytes */
   uint64_t node_bytes;     /* node buffer(s) */
   uint64_t prim_bytes;     /* leaf primitive buffer (+ index table if indirect) */
   uint64_t vert_bytes;     /* float4 vertex table */
@@ -58,6 +58,15 @@ scion_status scion_debug_host_stats(scion_host_bvh hb, scion_debug_info *info);
  *  leaf_ids[j]   : triangle id of leaf entry j (n_leaf_entries values). */
 scion_status scion_debug_host_decode(scion_host_bvh hb, uint32_t *kind, uint32_t *a, uint32_t *c,
                                      float *boxes, float *own_boxes, uint32_t *leaf_ids);
+
+/* Raw packed bytes: the node array (n_nodes * node_stride bytes), the second
+ * node array (node2_bytes; own-box SoA only) and the nine floats of the
+ * world grid of the quantised own-box codecs (q16: wlo.xyz, step.xyz, 0, 0,
+ * 0; eq10: wlo.xyz, whi.xyz, bin.xyz; zeros for other layouts), so a test can
+ * decode the codes on its own. SCION_ERR_INVALID_ARG if a capacity (bytes)
+ * is too small. */
+scion_status scion_debug_host_raw(scion_host_bvh hb, void *nodes, uint64_t nodes_cap, void *nodes2,
+                                  uint64_t nodes2_cap, float *frame);
 
 void scion_debug_host_destroy(scion_host_bvh hb);
 

@@ -21,13 +21,14 @@ CANDIDATE_LAYOUTS = {
     "bvh8_aos_u8": dict(width=8, box_layout="aos", box_prec="u8"),
 }
 # Traversal parameters the batched launch honours (child order). Plain
-# launches can also choose the fetch mode (per-lane fetch: rays_per_fetch=1).
+# launches can also choose the fetch mode (warp refill: rays_per_fetch=1..31).
 CANDIDATE_PARAMS = {"ordered": {}, "slot_order": {"ordered_children": 2},
                     "nearest_first": {"ordered_children": 3}}
 CANDIDATE_PARAMS_PLAIN = {**CANDIDATE_PARAMS,
-                          "ordered_lane_fetch": {"rays_per_fetch": 1},
-                          "slot_order_lane_fetch": {"ordered_children": 2, "rays_per_fetch": 1},
-                          "nearest_first_lane_fetch": {"ordered_children": 3, "rays_per_fetch": 1}}
+                          "ordered_refill1": {"rays_per_fetch": 1},
+                          "ordered_refill8": {"rays_per_fetch": 8},
+                          "slot_order_refill1": {"ordered_children": 2, "rays_per_fetch": 1},
+                          "nearest_first_refill1": {"ordered_children": 3, "rays_per_fetch": 1}}
 
 
 @dataclass

@@ -29,6 +29,7 @@ struct scion_bvh_s {
   bool indexed = false;
   uint32_t n_nodes = 0, node_stride = 0, n_leaf_entries = 0;
   uint32_t root_ref = kEmptyRef, depth = 0, stack_need = 0;
+  float frame[9] = {};  // world grid of the quantised own-box codecs
   uint64_t node_bytes = 0, node2_bytes = 0, prim_bytes = 0, idx_bytes = 0, vert_bytes = 0;
   void *d_nodes = nullptr, *d_nodes2 = nullptr, *d_prims = nullptr, *d_prim_ids = nullptr;
   void *d_verts = nullptr, *d_idx = nullptr;
@@ -105,10 +106,32 @@ scion_status upload(void **dst, const std::vector<T> &src, cudaStream_t s, uint6
   return SCION_OK;
 }
 
+// The BVH's part of the kernel arguments (buffers, root, codec constants).
+void bvh_args(const scion_bvh b, TraceArgs &a) {
+  a.nodes = static_cast<const uint4 *>(b->d_nodes);
+  a.nodes2 = static_cast<const uint2 *>(b->d_nodes2);
+  a.prims = static_cast<const float4 *>(b->d_prims);
+  a.prim_ids = static_cast<const uint32_t *>(b->d_prim_ids);
+  a.verts = static_cast<const float4 *>(b->d_verts);
+  a.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+  a.root_ref = b->root_ref;
+  a.n_nodes = b->n_nodes;
+  a.prim_indirect = b->desc.prim_ref;
+  a.node_stride = b->node_stride;
+  for (int k = 0; k < 9; ++k) a.frame[k] = b->frame[k];
+}
+
 TraceKernel pick_kernel(const scion_bvh b, int any, int stats) {
   const scion_layout_desc &d = b->desc;
   const int soa = (int)d.box_layout, cref = (int)d.child_ref;
-  if (b->own_box) return kernels_own(soa, cref, any, stats);
+  if (b->own_box) {
+    switch (d.box_prec) {
+      case PREC_F32: return kernels_own_p0(soa, cref, any, stats);
+      case PREC_Q16: return kernels_own_p3(soa, cref, any, stats);
+      case PREC_EQ10: return kernels_own_p4(soa, cref, any, stats);
+    }
+    return nullptr;
+  }
   switch (d.width * 10 + d.box_prec) {
     case 20: return kernels_w2_p0(soa, cref, any, stats);
     case 21: return kernels_w2_p1(soa, cref, any, stats);
@@ -232,7 +255,7 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
     return SCION_ERR_INVALID_ARG;
   scion_trace_params p{};
   if (params) p = *params;
-  if (p.reserved != 0 || p.reg_stack != 0 || (p.rays_per_fetch > 1 && p.rays_per_fetch != 32))
+  if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch > 32)
     return SCION_ERR_INVALID_ARG;
   uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
@@ -255,22 +278,14 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
     SCION_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
   TraceArgs a;
-  a.nodes = static_cast<const uint4 *>(b->d_nodes);
-  a.nodes2 = static_cast<const uint2 *>(b->d_nodes2);
-  a.prims = static_cast<const float4 *>(b->d_prims);
-  a.prim_ids = static_cast<const uint32_t *>(b->d_prim_ids);
-  a.verts = static_cast<const float4 *>(b->d_verts);
-  a.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+  bvh_args(b, a);
   a.rays = reinterpret_cast<const float4 *>(rays);
   a.out = out;
   a.n = n;
-  a.root_ref = b->root_ref;
-  a.n_nodes = b->n_nodes;
-  a.prim_indirect = b->desc.prim_ref;
   a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
   a.ordered = ordered;
   a.smem_stack = smem_entries;
-  a.lane_fetch = p.rays_per_fetch == 1 ? 1u : 0u;
+  a.refill_min = p.rays_per_fetch < 32 ? p.rays_per_fetch : 0u;
   const int slot = stream_slot(b, stream);
   if (slot < 0) {
     g_last_error = "more than 64 streams have traced this BVH";
@@ -304,6 +319,7 @@ scion_status upload_bvh(HostBVH &hb, uint64_t n_tris, uint64_t n_verts, bool ind
   b->root_ref = hb.root_ref;
   b->depth = hb.depth;
   b->stack_need = hb.stack_need;
+  for (int k = 0; k < 9; ++k) b->frame[k] = hb.frame[k];
   b->build_ms = hb.build_ms;
   cudaGetDevice(&b->device);
   uint64_t pb = 0, pi = 0;
@@ -526,22 +542,14 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
     }
     BatchScene sc{};
     TraceArgs &a = sc.a;
-    a.nodes = static_cast<const uint4 *>(b->d_nodes);
-    a.nodes2 = static_cast<const uint2 *>(b->d_nodes2);
-    a.prims = static_cast<const float4 *>(b->d_prims);
-    a.prim_ids = static_cast<const uint32_t *>(b->d_prim_ids);
-    a.verts = static_cast<const float4 *>(b->d_verts);
-    a.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+    bvh_args(b, a);
     a.rays = reinterpret_cast<const float4 *>(d_rays[i]);
     a.out = d_hits[i];
     a.n = n[i];
-    a.root_ref = b->root_ref;
-    a.n_nodes = b->n_nodes;
-    a.prim_indirect = b->desc.prim_ref;
     a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
     a.ordered = order_mode(p.ordered_children);
     a.smem_stack = bt->smem_stack;
-    a.lane_fetch = 0;
+    a.refill_min = 0;
     a.status = b->d_scratch + 3;
     sc.begin = total;
     sc.family = (uint32_t)fam;
@@ -669,7 +677,7 @@ scion_status scion_debug_host_stats(scion_host_bvh h, scion_debug_info *info) {
   info->depth = b.depth;
   info->stack_need = b.stack_need;
   info->own_box = b.own_box ? 1u : 0u;
-  info->reserved = 0;
+  info->node2_bytes = (uint32_t)b.nodes2.size();
   info->node_bytes = b.nodes.size() + b.nodes2.size();
   info->prim_bytes = host_prim_bytes(b);
   info->vert_bytes = b.verts4.size() * 4;
@@ -705,6 +713,18 @@ scion_status scion_debug_host_decode(scion_host_bvh h, uint32_t *kind, uint32_t 
     if (hb.desc.prim_ref == REF_DIRECT) std::memcpy(&leaf_ids[i], &hb.prim_direct[(size_t)i * 12 + 3], 4);
     else leaf_ids[i] = hb.prim_ids[i];
   }
+  return SCION_OK;
+}
+
+scion_status scion_debug_host_raw(scion_host_bvh h, void *nodes, uint64_t nodes_cap, void *nodes2,
+                                  uint64_t nodes2_cap, float *frame) {
+  if (!h || !frame) return SCION_ERR_INVALID_ARG;
+  const HostBVH &hb = h->hb;
+  if (nodes_cap < hb.nodes.size() || nodes2_cap < hb.nodes2.size()) return SCION_ERR_INVALID_ARG;
+  if ((!hb.nodes.empty() && !nodes) || (!hb.nodes2.empty() && !nodes2)) return SCION_ERR_INVALID_ARG;
+  if (!hb.nodes.empty()) std::memcpy(nodes, hb.nodes.data(), hb.nodes.size());
+  if (!hb.nodes2.empty()) std::memcpy(nodes2, hb.nodes2.data(), hb.nodes2.size());
+  for (int k = 0; k < 9; ++k) frame[k] = hb.frame[k];
   return SCION_OK;
 }
 
@@ -772,7 +792,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
     return SCION_ERR_INVALID_ARG;
   scion_trace_params p{};
   if (params) p = *params;
-  if (p.reserved != 0 || p.reg_stack != 0 || (p.rays_per_fetch > 1 && p.rays_per_fetch != 32) ||
+  if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch > 32 ||
       p.ordered_children > 3)
     return SCION_ERR_INVALID_ARG;
   const uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
@@ -800,22 +820,14 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
     SCION_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
   TraceArgs a;
-  a.nodes = static_cast<const uint4 *>(b->d_nodes);
-  a.nodes2 = static_cast<const uint2 *>(b->d_nodes2);
-  a.prims = static_cast<const float4 *>(b->d_prims);
-  a.prim_ids = static_cast<const uint32_t *>(b->d_prim_ids);
-  a.verts = static_cast<const float4 *>(b->d_verts);
-  a.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+  bvh_args(b, a);
   a.rays = reinterpret_cast<const float4 *>(rays);
   a.out = hits;
   a.n = n;
-  a.root_ref = b->root_ref;
-  a.n_nodes = b->n_nodes;
-  a.prim_indirect = b->desc.prim_ref;
   a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
   a.ordered = order_mode(p.ordered_children);
   a.smem_stack = smem_entries;
-  a.lane_fetch = p.rays_per_fetch == 1 ? 1u : 0u;
+  a.refill_min = p.rays_per_fetch < 32 ? p.rays_per_fetch : 0u;
   a.work = static_cast<unsigned long long *>(scratch);
   a.exit_count = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(scratch) + 8);
   a.status = b->d_scratch + 3;  // device errors still go to the BVH's status word

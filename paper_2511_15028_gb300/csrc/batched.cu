@@ -25,7 +25,7 @@ __device__ __forceinline__ void trace_one(const TraceArgs &a, Lane &L, Stack &st
       L.cur = kEmptyRef;
       break;
     }
-    if constexpr (OWN) step_bin<SOA, REF_DIRECT, false, false>(a, L, st, cnt);
+    if constexpr (OWN) step_bin<PREC_F32, SOA, REF_DIRECT, false, false>(a, L, st, cnt);
     else step_wide<W, PREC, SOA, REF_DIRECT, false, false>(a, L, st, cnt);
   }
 }

@@ -64,19 +64,125 @@ static uint16_t f16_directed(double x, int dir) {
 uint16_t f32_to_f16_down(float x) { return f16_directed(x, -1); }
 uint16_t f32_to_f16_up(float x) { return f16_directed(x, +1); }
 
+// Directed rounding of the exact value s + e to float (e is the error term
+// of an error-free transform, at most half an ulp of s): the nearest float to
+// s is at most one step away from the wanted one, and the comparison with
+// s + e decides the step exactly.
+static float round_dir(double s, double e, int dir) {
+  float f = (float)s;
+  if (std::isnan(f)) return f;
+  const bool above = (double)f > s || ((double)f == s && e < 0.0);
+  const bool below = (double)f < s || ((double)f == s && e > 0.0);
+  if (dir < 0 && above) f = std::nextafter(f, -INFINITY);
+  if (dir > 0 && below) f = std::nextafter(f, INFINITY);
+  return f;
+}
+// float products are exact in double (24 + 24 significant bits)
+float mul_rd_f32(float a, float b) { return round_dir((double)a * (double)b, 0.0, -1); }
+// a + b in double with Knuth's TwoSum error term
+static float add_dir(float a, float b, int dir) {
+  const double x = a, y = b, s = x + y;
+  if (!std::isfinite(s)) return (float)s;
+  const double bb = s - x, e = (x - (s - bb)) + (y - bb);
+  return round_dir(s, e, dir);
+}
+float add_rd_f32(float a, float b) { return add_dir(a, b, -1); }
+float sub_rd_f32(float a, float b) { return add_dir(a, -b, -1); }
+float sub_ru_f32(float a, float b) { return add_dir(a, -b, +1); }
+// largest float f with f * d <= n (n >= 0, d > 0 finite): the quotient
+// rounded toward -inf; f * d is exact in double
+static float div_rd_f32(float n, float d) {
+  float f = (float)((double)n / (double)d);
+  while (f > 0.0f && (double)f * (double)d > (double)n) f = std::nextafter(f, -INFINITY);
+  for (int i = 0; i < 4; ++i) {
+    const float g = std::nextafter(f, INFINITY);
+    if (std::isfinite(g) && (double)g * (double)d <= (double)n) f = g;
+    else break;
+  }
+  return f;
+}
+
+// ---- world-grid codecs of the quantised own-box node (q16, eq10)
+// q16: coordinate = fma(code, step, wlo), the device arithmetic.
+float q16_decode(uint32_t q, float step, float wlo) { return std::fma((float)q, step, wlo); }
+// fma with directed rounding: code * bin is exact in double (10 + 24 bits),
+// the sum with TwoSum
+static float fma_dir(double p, float c, int dir) {
+  const double y = c, s = p + y;
+  if (!std::isfinite(s)) return (float)s;
+  const double bb = s - p, e = (p - (s - bb)) + (y - bb);
+  return round_dir(s, e, dir);
+}
+// eq10: lo = rd(code * bin + wlo), hi = ru(whi - code * bin), one rounding each.
+float eq10_decode_lo(uint32_t q, float bin, float wlo) { return fma_dir((double)q * (double)bin, wlo, -1); }
+float eq10_decode_hi(uint32_t q, float bin, float whi) { return fma_dir(-(double)q * (double)bin, whi, +1); }
+
+// q16 frame of one axis: the smallest step (from extent / 65535 up) whose
+// last code reaches whi.
+static float q16_step(float wlo, float whi) {
+  const double ext = (double)whi - (double)wlo;
+  if (!(ext > 0.0)) return 0.0f;
+  float step = round_up_f32(ext / (double)kQ16Max);
+  while (q16_decode(kQ16Max, step, wlo) < whi) step = std::nextafter(step, INFINITY);
+  return step;
+}
+// eq10 frame of one axis (App. D.1 construct_bins_inverse / construct_bins):
+// bins_inv = rd(1023 / ru(whi - wlo)) (1 for an empty extent), bin = rd(1 / bins_inv).
+static void eq10_bins(float wlo, float whi, float *bin, float *bins_inv) {
+  float L = sub_ru_f32(whi, wlo);
+  if (!(L > 0.0f)) L = 1.0f;
+  *bins_inv = div_rd_f32((float)kEq10Max, L);
+  *bin = *bins_inv > 0.0f ? div_rd_f32(1.0f, *bins_inv) : 0.0f;
+}
+static uint32_t clamp_code(double v, uint32_t qmax) {
+  if (!(v > 0.0)) return 0;
+  if (v >= (double)qmax) return qmax;
+  return (uint32_t)v;
+}
+// Codes of one axis of a box; the decoded interval always encloses [lo, hi]
+// (verify-and-bump against the exact device decode). Returns false if not.
+static bool q16_codes(float lo, float hi, float step, float wlo, uint32_t *qlo, uint32_t *qhi) {
+  uint32_t a = 0, b = 0;
+  if (step > 0.0f) {
+    a = clamp_code(std::floor(((double)lo - (double)wlo) / (double)step), kQ16Max);
+    b = clamp_code(std::ceil(((double)hi - (double)wlo) / (double)step), kQ16Max);
+  }
+  while (a > 0 && q16_decode(a, step, wlo) > lo) --a;
+  while (b < kQ16Max && q16_decode(b, step, wlo) < hi) ++b;
+  *qlo = a;
+  *qhi = b;
+  return q16_decode(a, step, wlo) <= lo && q16_decode(b, step, wlo) >= hi;
+}
+// eq10 codes: the App. D.1 quantize_lo / quantize_hi (floor of the directed
+// products), then verify-and-bump; hi codes count down from whi.
+static bool eq10_codes(float lo, float hi, float bin, float bins_inv, float wlo, float whi, uint32_t *qlo,
+                       uint32_t *qhi) {
+  uint32_t a = clamp_code(std::floor((double)mul_rd_f32(sub_rd_f32(lo, wlo), bins_inv)), kEq10Max);
+  uint32_t b = clamp_code(std::floor((double)mul_rd_f32(sub_rd_f32(whi, hi), bins_inv)), kEq10Max);
+  while (a > 0 && eq10_decode_lo(a, bin, wlo) > lo) --a;
+  while (b > 0 && eq10_decode_hi(b, bin, whi) < hi) --b;
+  *qlo = a;
+  *qhi = b;
+  return eq10_decode_lo(a, bin, wlo) <= lo && eq10_decode_hi(b, bin, whi) >= hi;
+}
+
 // ------------------------------------------------------------ descriptor
 scion_status normalize_desc(const scion_layout_desc &in, scion_layout_desc *out, bool *own_box) {
   scion_layout_desc d = in;
-  if (d.reserved != 0) return SCION_ERR_INVALID_ARG;
+  if (d.align != 0 && d.align != 16) return SCION_ERR_INVALID_ARG;
   if (d.width != 2 && d.width != 4 && d.width != 8) return SCION_ERR_UNSUPPORTED_LAYOUT;
-  if (d.box_layout > 1 || d.box_prec > 2 || d.child_ref > 1 || d.prim_ref > 1 || d.order > 2)
+  if (d.box_layout > 1 || d.box_prec > PREC_EQ10 || d.child_ref > 1 || d.prim_ref > 1 || d.order > 2)
     return SCION_ERR_UNSUPPORTED_LAYOUT;
   if (d.leaf_max == 0) d.leaf_max = 4;
   if (d.leaf_max > kMaxLeaf) return SCION_ERR_UNSUPPORTED_LAYOUT;
   if (d.sah_bins == 0) d.sah_bins = 16;
   if (d.sah_bins < 2 || d.sah_bins > 64) return SCION_ERR_UNSUPPORTED_LAYOUT;
   if (d.treelet_bytes == 0) d.treelet_bytes = 1024;
-  const bool ob = d.width == 2 && d.box_prec == PREC_F32;
+  if (prec_is_world_grid(d.box_prec)) {
+    if (d.width != 2 || d.leaf_max > kQMaxLeaf) return SCION_ERR_UNSUPPORTED_LAYOUT;
+    if (d.box_prec == PREC_EQ10 && d.box_layout == LAYOUT_SOA) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  }
+  const bool ob = d.width == 2 && (d.box_prec == PREC_F32 || prec_is_world_grid(d.box_prec));
   if (ob && d.child_ref == REF_DIRECT && d.order != ORDER_DFS) return SCION_ERR_UNSUPPORTED_LAYOUT;
   *out = d;
   *own_box = ob;
@@ -670,10 +776,39 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
     for (size_t pi = 0; pi < nl; ++pi) pbase[pi] = lb.nodes[ord[pi]].count;
     alloc_prims(out, exclusive_scan(pbase));
     out->n_nodes = (uint32_t)nl;
-    const bool soa = desc.box_layout == LAYOUT_SOA;
-    out->node_stride = soa ? kBinBoxBytes : kBinNodeBytes;
+    const uint32_t prec = desc.box_prec;
+    const bool soa = desc.box_layout == LAYOUT_SOA, a16 = desc.align == 16;
+    const bool quant = prec_is_world_grid(prec);
+    if (quant && nl >= kQMaxNodes) {
+      *err = "too many nodes for the quantised own-box node";
+      return SCION_ERR_UNSUPPORTED_LAYOUT;
+    }
+    uint32_t ref_bytes = 0;  // SoA word/ref array element
+    if (!quant) {
+      out->node_stride = soa ? (a16 ? 32u : kBinBoxBytes) : kBinNodeBytes;
+      ref_bytes = soa ? kBinRefBytes : 0u;
+    } else if (prec == PREC_Q16) {
+      out->node_stride = soa ? (a16 ? 16u : kQBoxBytes) : 16u;
+      ref_bytes = soa ? 4u : 0u;
+    } else {
+      out->node_stride = a16 ? 16u : kQBoxBytes;
+    }
     out->nodes.assign((size_t)nl * out->node_stride, 0);
-    if (soa) out->nodes2.assign((size_t)nl * kBinRefBytes, 0);
+    if (ref_bytes) out->nodes2.assign((size_t)nl * ref_bytes, 0);
+    // world grid over the padded root box: q16 {wlo, step}, eq10 {wlo, whi, bin}
+    float bins_inv[3] = {0.f, 0.f, 0.f};
+    if (quant) {
+      const Box3 root = padded(lb.nodes[0].box);
+      for (int a = 0; a < 3; ++a) {
+        out->frame[a] = root.lo[a];
+        if (prec == PREC_Q16) {
+          out->frame[3 + a] = q16_step(root.lo[a], root.hi[a]);
+        } else {
+          out->frame[3 + a] = root.hi[a];
+          eq10_bins(root.lo[a], root.hi[a], &out->frame[6 + a], &bins_inv[a]);
+        }
+      }
+    }
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (long long pi = 0; pi < (long long)nl; ++pi) {
@@ -696,17 +831,44 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
         meta = bin_pack_meta(0, nd.axis);
       }
       uint8_t *p = out->nodes.data() + pi * out->node_stride;
-      for (int a = 0; a < 3; ++a) {
-        put_f32(p + 4 * a, b.lo[a]);
-        put_f32(p + 12 + 4 * a, b.hi[a]);
+      if (!quant) {
+        for (int a = 0; a < 3; ++a) {
+          put_f32(p + 4 * a, b.lo[a]);
+          put_f32(p + 12 + 4 * a, b.hi[a]);
+        }
+        uint8_t *q = soa ? out->nodes2.data() + pi * kBinRefBytes : p + 24;
+        put_u32(q, ref);
+        put_u32(q + 4, meta);
+        continue;
       }
-      uint8_t *q = soa ? out->nodes2.data() + pi * kBinRefBytes : p + 24;
-      put_u32(q, ref);
-      put_u32(q + 4, meta);
+      const uint32_t word = nd.count > 0 ? qbin_leaf(ref, nd.count) : qbin_interior(ref, nd.axis);
+      uint32_t qlo[3], qhi[3];
+      for (int a = 0; a < 3; ++a) {
+        const bool ok = prec == PREC_Q16
+                            ? q16_codes(b.lo[a], b.hi[a], out->frame[3 + a], out->frame[a], &qlo[a], &qhi[a])
+                            : eq10_codes(b.lo[a], b.hi[a], out->frame[6 + a], bins_inv[a], out->frame[a],
+                                         out->frame[3 + a], &qlo[a], &qhi[a]);
+        bad |= ok ? 0 : 2;
+      }
+      if (prec == PREC_Q16) {
+        for (int a = 0; a < 3; ++a) {
+          put_u16(p + 2 * a, (uint16_t)qlo[a]);
+          put_u16(p + 6 + 2 * a, (uint16_t)qhi[a]);
+        }
+        put_u32(soa ? out->nodes2.data() + pi * 4 : p + 12, word);
+      } else {
+        put_u32(p, eq10_pack(qlo[0], qlo[1], qlo[2]));
+        put_u32(p + 4, eq10_pack(qhi[0], qhi[1], qhi[2]));
+        put_u32(p + 8, word);
+      }
     }
-    if (bad) {
+    if (bad & 1) {
       *err = "node order violates the child reference encoding";
       return SCION_ERR_UNSUPPORTED_LAYOUT;
+    }
+    if (bad & 2) {
+      *err = "world-grid enclosure";
+      return SCION_ERR_BAD_INPUT;
     }
     out->root_ref = 0;
     out->depth = tree_depth(t, ord);
@@ -926,13 +1088,34 @@ int decode_node(const HostBVH &b, uint32_t node, DecodedChild *ch, Box3 *own) {
   if (b.own_box) {
     const bool soa = d.box_layout == LAYOUT_SOA;
     const uint8_t *p = b.nodes.data() + (size_t)node * b.node_stride;
-    const uint8_t *q = soa ? b.nodes2.data() + (size_t)node * kBinRefBytes : p + 24;
-    for (int a = 0; a < 3; ++a) {
-      own->lo[a] = get_f32(p + 4 * a);
-      own->hi[a] = get_f32(p + 12 + 4 * a);
+    uint32_t ref, cnt;
+    if (d.box_prec == PREC_F32) {
+      const uint8_t *q = soa ? b.nodes2.data() + (size_t)node * kBinRefBytes : p + 24;
+      for (int a = 0; a < 3; ++a) {
+        own->lo[a] = get_f32(p + 4 * a);
+        own->hi[a] = get_f32(p + 12 + 4 * a);
+      }
+      ref = get_u32(q);
+      cnt = bin_meta_count(get_u32(q + 4));
+    } else {
+      uint32_t word;
+      if (d.box_prec == PREC_Q16) {
+        for (int a = 0; a < 3; ++a) {
+          own->lo[a] = q16_decode(get_u16(p + 2 * a), b.frame[3 + a], b.frame[a]);
+          own->hi[a] = q16_decode(get_u16(p + 6 + 2 * a), b.frame[3 + a], b.frame[a]);
+        }
+        word = get_u32(soa ? b.nodes2.data() + (size_t)node * 4 : p + 12);
+      } else {
+        const uint32_t wl = get_u32(p), wh = get_u32(p + 4);
+        for (int a = 0; a < 3; ++a) {
+          own->lo[a] = eq10_decode_lo(eq10_code(wl, a), b.frame[6 + a], b.frame[a]);
+          own->hi[a] = eq10_decode_hi(eq10_code(wh, a), b.frame[6 + a], b.frame[3 + a]);
+        }
+        word = get_u32(p + 8);
+      }
+      cnt = qbin_count(word);
+      ref = cnt > 0 ? qbin_first(word) : qbin_field(word);
     }
-    const uint32_t ref = get_u32(q), meta = get_u32(q + 4);
-    const uint32_t cnt = bin_meta_count(meta);
     if (cnt > 0) {
       ch[0].kind = 2;
       ch[0].first = ref;

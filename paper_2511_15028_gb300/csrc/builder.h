@@ -43,7 +43,7 @@ struct WNode {
 
 struct HostBVH {
   scion_layout_desc desc;
-  bool own_box = false;             // width-2 f32 own-box node
+  bool own_box = false;             // width-2 own-box node (f32, q16, eq10)
   uint32_t n_tris = 0, n_verts = 0;
   bool indexed = false;
   std::vector<uint8_t> nodes;       // node buffer (AoS nodes or SoA boxes)
@@ -58,6 +58,7 @@ struct HostBVH {
   uint32_t root_ref = kEmptyRef;    // wide: encoded ref of the root; own-box: 0
   uint32_t depth = 0;               // levels of the stored tree
   uint32_t stack_need = 0;          // worst-case traversal stack entries
+  float frame[9] = {};              // world grid: q16 {wlo, step}, eq10 {wlo, whi, bin}
   double build_ms = 0.0;
 };
 
@@ -84,6 +85,15 @@ float round_up_f32(double x);
 uint16_t f32_to_f16_down(float x);
 uint16_t f32_to_f16_up(float x);
 float f16_to_f32(uint16_t h);
+// Exact emulation of the device's directed-rounding float ops, and the
+// world-grid decodes of the quantised own-box node (same results as the GPU).
+float mul_rd_f32(float a, float b);
+float add_rd_f32(float a, float b);
+float sub_rd_f32(float a, float b);
+float sub_ru_f32(float a, float b);
+float q16_decode(uint32_t q, float step, float wlo);
+float eq10_decode_lo(uint32_t q, float bin, float wlo);
+float eq10_decode_hi(uint32_t q, float bin, float whi);
 
 // Decode one packed node back to its logical view (round-trip check).
 struct DecodedChild {

@@ -8,10 +8,13 @@ namespace scion {
 typedef void (*TraceKernel)(TraceArgs);
 
 // Defined by trace_inst.cu, compiled once per node family:
-//   own-box binary node       : kernels_own(soa, cref, any, stats)
+//   own-box binary node       : kernels_own_p<prec>(soa, cref, any, stats),
+//                               prec 0 f32, 3 q16, 4 eq10
 //   wide node of width W, prec: kernels_w<W>_p<prec>(soa, cref, any, stats)
 // stats = 1 selects the counting variant (visit counters, same results).
-TraceKernel kernels_own(int soa, int cref, int any, int stats);
+TraceKernel kernels_own_p0(int soa, int cref, int any, int stats);
+TraceKernel kernels_own_p3(int soa, int cref, int any, int stats);
+TraceKernel kernels_own_p4(int soa, int cref, int any, int stats);
 TraceKernel kernels_w2_p0(int soa, int cref, int any, int stats);
 TraceKernel kernels_w2_p1(int soa, int cref, int any, int stats);
 TraceKernel kernels_w2_p2(int soa, int cref, int any, int stats);
@@ -23,5 +26,14 @@ TraceKernel kernels_w8_p1(int soa, int cref, int any, int stats);
 TraceKernel kernels_w8_p2(int soa, int cref, int any, int stats);
 
 constexpr int kMaxThreadsPerBlock = 256;
+// Four 256-thread CTAs per SM: caps a traversal kernel at 64 registers so 32
+// warps per SM keep dependent node loads in flight (the 8-wide f16/u8 kernels
+// otherwise take 74-80 registers, and 24 warps). The 8-wide f32 node (48
+// floats of boxes) would spill heavily under the cap and keeps its own count.
+#if defined(SCION_W) && SCION_W == 8 && SCION_PREC == 0
+constexpr int kMinBlocksPerSm = 1;
+#else
+constexpr int kMinBlocksPerSm = 4;
+#endif
 
 }  // namespace scion

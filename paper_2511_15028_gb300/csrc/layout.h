@@ -14,6 +14,22 @@
 //      child_ref indirect: left = ref, right = ref + 1 (siblings contiguous).
 //      leaf              : prims [ref, ref + count).
 //
+//  * Quantised own-box binary node (the world-frame bvh2 codecs of Table 1,
+//    Section 9.2.5 and App. D.1/D.3): the same tree with the node's box stored
+//    as integer codes on one grid spanning the (padded) root box, and one u32
+//    word: bits 0-3 primitive count (0 = interior); interior: bits 4-5 split
+//    axis, bits 6-31 right offset (direct) or left index (indirect); leaf:
+//    bits 4-31 first prim. Limits: leaf_max <= 15, nodes < 2^26.
+//      q16  ("sg-pbrt-q16"): 6 x u16 codes (lo.xyz, hi.xyz) + word = 16 B;
+//           coordinate = fma(code, step[a], wlo[a]) (one rounding).
+//           SoA ("-soaos"): 12 B code array (16 B with align 16) + u32 words.
+//      eq10 ("sg-eq"): u32 lo codes (x << 20 | y << 10 | z, counted up from
+//           wlo), u32 hi codes (same packing, counted down from whi), word =
+//           12 B (16 B with align 16); lo = rd(code * bin + wlo),
+//           hi = ru(whi - code * bin), each one fused multiply-add rounded
+//           outward (App. D.1 rounds the product and the sum separately;
+//           the fused form is one instruction and never looser).
+//
 //  * Children-in-parent wide node (width W = 2, 4, 8; the 8-ary layouts of
 //    Table 1, App. D.2). It holds the W child boxes and W child references:
 //      [header (u8 only, 16 B)] [boxes] [references], padded to 32 B.
@@ -47,7 +63,7 @@
 
 namespace scion {
 
-enum BoxPrec : uint32_t { PREC_F32 = 0, PREC_F16 = 1, PREC_U8 = 2 };
+enum BoxPrec : uint32_t { PREC_F32 = 0, PREC_F16 = 1, PREC_U8 = 2, PREC_Q16 = 3, PREC_EQ10 = 4 };
 enum { LAYOUT_AOS = 0, LAYOUT_SOA = 1 };
 enum { REF_DIRECT = 0, REF_INDIRECT = 1 };
 enum { ORDER_DFS = 0, ORDER_BFS = 1, ORDER_TREELET = 2 };
@@ -99,6 +115,21 @@ constexpr uint32_t kBinRefBytes = 8;    // SoA ref array element
 SCION_HD uint32_t bin_pack_meta(uint32_t count, uint32_t axis) { return (count & 0xFFFFu) | (axis << 16); }
 SCION_HD uint32_t bin_meta_count(uint32_t m) { return m & 0xFFFFu; }
 SCION_HD uint32_t bin_meta_axis(uint32_t m) { return (m >> 16) & 3u; }
+
+// ---- quantised own-box binary node (q16 / eq10)
+constexpr uint32_t kQBoxBytes = 12;       // 6 x u16, or 2 x u32 + word (eq10 AoS)
+constexpr uint32_t kQMaxLeaf = 15;
+constexpr uint32_t kQMaxNodes = 1u << 26;
+constexpr uint32_t kQ16Max = 65535u, kEq10Max = 1023u;
+SCION_HD uint32_t qbin_leaf(uint32_t first, uint32_t count) { return (first << 4) | count; }
+SCION_HD uint32_t qbin_interior(uint32_t field, uint32_t axis) { return (field << 6) | (axis << 4); }
+SCION_HD uint32_t qbin_count(uint32_t w) { return w & 15u; }
+SCION_HD uint32_t qbin_axis(uint32_t w) { return (w >> 4) & 3u; }
+SCION_HD uint32_t qbin_field(uint32_t w) { return w >> 6; }
+SCION_HD uint32_t qbin_first(uint32_t w) { return w >> 4; }
+SCION_HD uint32_t eq10_pack(uint32_t x, uint32_t y, uint32_t z) { return (x << 20) | (y << 10) | z; }
+SCION_HD uint32_t eq10_code(uint32_t w, int axis) { return (w >> (20 - 10 * axis)) & 1023u; }
+SCION_HD bool prec_is_world_grid(uint32_t prec) { return prec == PREC_Q16 || prec == PREC_EQ10; }
 
 constexpr uint32_t kPrimDirectBytes = 48;
 

@@ -45,11 +45,13 @@ struct TraceArgs {
   uint32_t max_steps;
   uint32_t ordered;         // 0 slot order, 1 sorted by entry distance, 2 nearest first
   uint32_t smem_stack;      // shared-memory stack entries per thread
-  uint32_t lane_fetch;      // 0: 32-ray warp batches, 1: per-lane fetch
+  uint32_t refill_min;      // 0: 32-ray warp batches; k: refill once k lanes idle
   unsigned long long *work; // persistent work counter (self-resetting)
   uint32_t *exit_count;     // CTAs finished (self-resetting)
   uint32_t *status;         // first device error code
   unsigned long long *stats;  // counting kernels: nodes, leaves, prim tests, rays
+  uint32_t node_stride;     // own-box node (or SoA box record) bytes
+  float frame[9];           // world grid of q16 {wlo, step} / eq10 {wlo, whi, bin}
 };
 
 // Per-thread visit counters of the counting (STATS) kernels.
@@ -299,6 +301,14 @@ struct WideNode {
     if (kElem == 2) return (w >> ((off & 3) * 8)) & 0xFFFFu;
     return (w >> ((off & 3) * 8)) & 0xFFu;
   }
+  // u8 code of coordinate c of child k as a float, exactly: a byte permute
+  // puts the code into the low mantissa bits of 2^23, then 2^23 is taken off
+  // (full-rate integer/float ops instead of an integer-to-float conversion)
+  static __device__ __forceinline__ float code(const uint4 (&q)[NQ], int k, int c) {
+    const int off = box_off(k, c);
+    const uint32_t w = qword(q, off >> 2);
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(off & 3))) - 8388608.0f;
+  }
 };
 
 // Per-lane traversal state that survives between steps, so that a lane can
@@ -403,11 +413,11 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
       float tn;
       bool hit;
       if (PREC == PREC_U8) {
-        const uint32_t lx = N::raw(q, k, 0), ly = N::raw(q, k, 1), lz = N::raw(q, k, 2);
-        const uint32_t hx = N::raw(q, k, 3), hy = N::raw(q, k, 4), hz = N::raw(q, k, 5);
-        const float nqx = (float)(r.nx ? hx : lx), fqx = (float)(r.nx ? lx : hx);
-        const float nqy = (float)(r.ny ? hy : ly), fqy = (float)(r.ny ? ly : hy);
-        const float nqz = (float)(r.nz ? hz : lz), fqz = (float)(r.nz ? lz : hz);
+        const float lx = N::code(q, k, 0), ly = N::code(q, k, 1), lz = N::code(q, k, 2);
+        const float hx = N::code(q, k, 3), hy = N::code(q, k, 4), hz = N::code(q, k, 5);
+        const float nqx = r.nx ? hx : lx, fqx = r.nx ? lx : hx;
+        const float nqy = r.ny ? hy : ly, fqy = r.ny ? ly : hy;
+        const float nqz = r.nz ? hz : lz, fqz = r.nz ? lz : hz;
         hit = slab_t(r, fmaf(nqx, ax, bx), fmaf(nqy, ay, by), fmaf(nqz, az, bz), fmaf(fqx, ax, bx),
                      fmaf(fqy, ay, by), fmaf(fqz, az, bz), tlim, tn);
       } else {
@@ -458,34 +468,88 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
   }
 }
 
+// Exact small-integer to float conversions with full-rate integer ops: the
+// code goes into the low mantissa bits of 2^23, then 2^23 is subtracted.
+__device__ __forceinline__ float u16lo_f(uint32_t w) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7410u)) - 8388608.0f;
+}
+__device__ __forceinline__ float u16hi_f(uint32_t w) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7432u)) - 8388608.0f;
+}
+__device__ __forceinline__ float eq10_f(uint32_t w, int axis) {
+  return __uint_as_float(0x4B000000u | eq10_code(w, axis)) - 8388608.0f;
+}
+
 // One step of the own-box binary traversal (pbrt LinearBVH, Fig. 4b): test
 // the node's own box; a leaf tests its triangles, an interior node pushes its
 // far child (by the split axis and the ray direction) and continues near.
-template <int SOA, int CREF, bool ANY, bool STATS>
+// PREC selects the box codec: f32 corners, or world-grid codes decoded
+// exactly as the packer verified them (q16: fma(code, step, wlo); eq10: one
+// fused multiply-add rounded outward per coordinate) before the f32 slab test.
+template <int PREC, int SOA, int CREF, bool ANY, bool STATS>
 __device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, Stack &st, Counts &cnt) {
   const Ray &r = L.r;
   const uint32_t cur = L.cur;
   if (STATS) cnt.nodes++;
   float lo0, lo1, lo2, hi0, hi1, hi2;
-  uint32_t ref, meta;
-  if (SOA) {
-    const uint2 *bp = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(a.nodes) +
-                                                      (size_t)cur * kBinBoxBytes);
-    const uint2 b0 = __ldg(bp), b1 = __ldg(bp + 1), b2 = __ldg(bp + 2);
-    const uint2 rm = __ldg(a.nodes2 + cur);
-    lo0 = __uint_as_float(b0.x); lo1 = __uint_as_float(b0.y); lo2 = __uint_as_float(b1.x);
-    hi0 = __uint_as_float(b1.y); hi1 = __uint_as_float(b2.x); hi2 = __uint_as_float(b2.y);
-    ref = rm.x; meta = rm.y;
+  uint32_t field, n, axis;  // child reference / first prim, prim count, split axis
+  if (PREC == PREC_F32) {
+    uint32_t ref, meta;
+    if (SOA) {
+      const uint2 *bp = reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(a.nodes) +
+                                                        (size_t)cur * a.node_stride);
+      const uint2 b0 = __ldg(bp), b1 = __ldg(bp + 1), b2 = __ldg(bp + 2);
+      const uint2 rm = __ldg(a.nodes2 + cur);
+      lo0 = __uint_as_float(b0.x); lo1 = __uint_as_float(b0.y); lo2 = __uint_as_float(b1.x);
+      hi0 = __uint_as_float(b1.y); hi1 = __uint_as_float(b2.x); hi2 = __uint_as_float(b2.y);
+      ref = rm.x; meta = rm.y;
+    } else {
+      const uint4 q0 = ldg4(a.nodes + 2 * (size_t)cur), q1 = ldg4(a.nodes + 2 * (size_t)cur + 1);
+      lo0 = __uint_as_float(q0.x); lo1 = __uint_as_float(q0.y); lo2 = __uint_as_float(q0.z);
+      hi0 = __uint_as_float(q0.w); hi1 = __uint_as_float(q1.x); hi2 = __uint_as_float(q1.y);
+      ref = q1.z; meta = q1.w;
+    }
+    field = ref;
+    n = bin_meta_count(meta);
+    axis = bin_meta_axis(meta);
   } else {
-    const uint4 q0 = ldg4(a.nodes + 2 * (size_t)cur), q1 = ldg4(a.nodes + 2 * (size_t)cur + 1);
-    lo0 = __uint_as_float(q0.x); lo1 = __uint_as_float(q0.y); lo2 = __uint_as_float(q0.z);
-    hi0 = __uint_as_float(q0.w); hi1 = __uint_as_float(q1.x); hi2 = __uint_as_float(q1.y);
-    ref = q1.z; meta = q1.w;
+    const char *np = reinterpret_cast<const char *>(a.nodes) + (size_t)cur * a.node_stride;
+    uint32_t w0, w1, w2, w3 = 0;
+    if (a.node_stride == 16) {
+      const uint4 v = ldg4(reinterpret_cast<const uint4 *>(np));
+      w0 = v.x; w1 = v.y; w2 = v.z; w3 = v.w;
+    } else {
+      const uint32_t *wp = reinterpret_cast<const uint32_t *>(np);
+      w0 = __ldg(wp); w1 = __ldg(wp + 1); w2 = __ldg(wp + 2);
+    }
+    uint32_t word;
+    if (PREC == PREC_Q16) {
+      // codes: w0 = lo.x | lo.y << 16, w1 = lo.z | hi.x << 16, w2 = hi.y | hi.z << 16
+      word = SOA ? __ldg(reinterpret_cast<const uint32_t *>(a.nodes2) + cur) : w3;
+      lo0 = fmaf(u16lo_f(w0), a.frame[3], a.frame[0]);
+      lo1 = fmaf(u16hi_f(w0), a.frame[4], a.frame[1]);
+      lo2 = fmaf(u16lo_f(w1), a.frame[5], a.frame[2]);
+      hi0 = fmaf(u16hi_f(w1), a.frame[3], a.frame[0]);
+      hi1 = fmaf(u16lo_f(w2), a.frame[4], a.frame[1]);
+      hi2 = fmaf(u16hi_f(w2), a.frame[5], a.frame[2]);
+    } else {
+      // w0 = lo codes counted up from wlo, w1 = hi codes counted down from whi
+      word = w2;
+      lo0 = __fmaf_rd(eq10_f(w0, 0), a.frame[6], a.frame[0]);
+      lo1 = __fmaf_rd(eq10_f(w0, 1), a.frame[7], a.frame[1]);
+      lo2 = __fmaf_rd(eq10_f(w0, 2), a.frame[8], a.frame[2]);
+      hi0 = __fmaf_ru(-eq10_f(w1, 0), a.frame[6], a.frame[3]);
+      hi1 = __fmaf_ru(-eq10_f(w1, 1), a.frame[7], a.frame[4]);
+      hi2 = __fmaf_ru(-eq10_f(w1, 2), a.frame[8], a.frame[5]);
+    }
+    n = qbin_count(word);
+    axis = qbin_axis(word);
+    field = n > 0 ? qbin_first(word) : qbin_field(word);
   }
   const float tlim = ANY ? r.tmax : fminf(r.tmax, L.b.t);
   float tn;
   if (slab(r, lo0, lo1, lo2, hi0, hi1, hi2, tlim, tn)) {
-    const uint32_t n = bin_meta_count(meta);
+    const uint32_t ref = field;
     if (n > 0) {
       if (visit_leaf<ANY, STATS>(a, r, ref, n, L.b, cnt)) {
         L.found = true;
@@ -495,8 +559,7 @@ __device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, Stack &st,
     } else {
       const uint32_t l = CREF == REF_DIRECT ? cur + 1 : ref;
       const uint32_t rr = CREF == REF_DIRECT ? cur + ref : ref + 1;
-      const uint32_t ax = bin_meta_axis(meta);
-      const bool neg = ax == 0 ? r.nx : (ax == 1 ? r.ny : r.nz);
+      const bool neg = axis == 0 ? r.nx : (axis == 1 ? r.ny : r.nz);
       const bool swap = !ANY && a.ordered && neg;
       if (!st.push(swap ? l : rr, 0.0f)) { L.err = kErrStack; L.cur = kEmptyRef; return; }
       L.cur = swap ? rr : l;
@@ -516,7 +579,7 @@ __device__ __forceinline__ void trace_lane(const TraceArgs &a, Lane &L, Stack &s
       L.cur = kEmptyRef;
       break;
     }
-    if constexpr (OWN) step_bin<SOA, CREF, ANY, STATS>(a, L, st, cnt);
+    if constexpr (OWN) step_bin<PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
     else step_wide<W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
   }
 }
@@ -575,50 +638,68 @@ __device__ __forceinline__ void body_warp_batch(const TraceArgs &a, Stack &st) {
   }
 }
 
-// Per-lane ray fetch. The rays are cut into 32-ray
-// blocks dealt to the CTAs round-robin (CTA c owns blocks c, c + G, c + 2G,
-// ... for a grid of G CTAs), so every CTA sees a spatially uniform share and
-// no global atomic is needed. Inside a CTA a shared counter hands out the
-// CTA's rays one at a time: a lane takes its next ray the moment it finishes
-// the previous one, so a warp never idles on its slowest ray.
+// Refilled warps. The rays are cut into 32-ray blocks dealt to the CTAs
+// round-robin (CTA c owns blocks c, c + G, c + 2G, ... for a grid of G CTAs),
+// so every CTA sees a spatially uniform share and no global atomic is needed.
+// A lane whose ray is finished idles until at least `refill_min` lanes of its
+// warp are idle; then the warp takes that many consecutive rays of its CTA's
+// share with one shared-memory atomicAdd and the idle lanes set them up
+// together (refill_min = 1: a lane is refilled at the next step).
 template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ void body_lane_fetch(const TraceArgs &a, Stack &st) {
+__device__ __forceinline__ void body_refill(const TraceArgs &a, Stack &st) {
   __shared__ uint32_t cta_next;
   if (threadIdx.x == 0) cta_next = 0;
   __syncthreads();
   Counts cnt;
   uint32_t n_rays = 0;
   const unsigned long long G = gridDim.x, c = blockIdx.x;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t below = (1u << lane) - 1u;  // lanes ranked before this one
   Lane L;
   L.cur = kEmptyRef;
-  bool has_ray = false;
+  bool has_ray = false, exhausted = false;  // exhausted: warp-uniform
   while (true) {
-    if (!has_ray) {
-      const uint32_t j = atomicAdd(&cta_next, 1u);
-      const unsigned long long rid = (c + (unsigned long long)(j >> 5) * G) * 32ull + (j & 31u);
-      if (rid >= a.n) break;
-      L.rid = rid;
-      setup_ray(ldg4f(a.rays + 2 * rid), ldg4f(a.rays + 2 * rid + 1), L.r);
-      L.b = Best{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_MISS};
-      L.steps = 0;
-      L.err = 0;
-      L.found = false;
-      st.sp = 0;
-      if constexpr (OWN) L.cur = a.n_nodes > 0 ? 0u : kEmptyRef;
-      else L.cur = a.root_ref;
-      has_ray = true;
-      if (STATS) n_rays++;
+    const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !has_ray);
+    const uint32_t k = __popc(idle);
+    if (!exhausted && k >= a.refill_min) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&cta_next, k);
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      // ray ids grow with the index, so the last index decides exhaustion
+      const uint32_t jl = base + k - 1u;
+      exhausted = (c + (unsigned long long)(jl >> 5) * G) * 32ull + (jl & 31u) >= a.n;
+      if (!has_ray) {
+        const uint32_t j = base + __popc(idle & below);
+        const unsigned long long rid = (c + (unsigned long long)(j >> 5) * G) * 32ull + (j & 31u);
+        if (rid < a.n) {
+          L.rid = rid;
+          setup_ray(ldg4f(a.rays + 2 * rid), ldg4f(a.rays + 2 * rid + 1), L.r);
+          L.b = Best{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_MISS};
+          L.steps = 0;
+          L.err = 0;
+          L.found = false;
+          st.sp = 0;
+          if constexpr (OWN) L.cur = a.n_nodes > 0 ? 0u : kEmptyRef;
+          else L.cur = a.root_ref;
+          has_ray = true;
+          if (STATS) n_rays++;
+        }
+      }
     }
-    if (L.cur != kEmptyRef) {
+    if (__ballot_sync(0xFFFFFFFFu, has_ray) == 0u) {
+      if (exhausted) break;
+      continue;
+    }
+    if (has_ray && L.cur != kEmptyRef) {
       if (++L.steps > a.max_steps) {
         L.err = kErrIter;
         L.cur = kEmptyRef;
       } else {
-        if constexpr (OWN) step_bin<SOA, CREF, ANY, STATS>(a, L, st, cnt);
+        if constexpr (OWN) step_bin<PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
         else step_wide<W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
       }
     }
-    if (L.cur == kEmptyRef) {
+    if (has_ray && L.cur == kEmptyRef) {
       if (L.err) atomicCAS(a.status, 0u, L.err);
       if (ANY) {
         static_cast<uint32_t *>(a.out)[L.rid] = L.err ? SCION_PRIM_ERROR : (L.found ? 1u : 0u);
@@ -647,7 +728,7 @@ __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
   st.stride = blockDim.x;
   st.cap_sh = (int)a.smem_stack;
   st.sp = 0;
-  if (a.lane_fetch) body_lane_fetch<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, st);
+  if (a.refill_min) body_refill<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, st);
   else body_warp_batch<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, st);
 }
 

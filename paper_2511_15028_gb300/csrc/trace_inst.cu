@@ -1,6 +1,7 @@
 // Instantiates the traversal kernels of one node family. Compiled several
-// times with -DSCION_OWN=1, or -DSCION_W=<2|4|8> -DSCION_PREC=<0|1|2>, so the
-// families build in parallel.
+// times with -DSCION_OWN=1 -DSCION_PREC=<0|3|4> (own-box node with f32, q16
+// or eq10 boxes), or -DSCION_W=<2|4|8> -DSCION_PREC=<0|1|2>, so the families
+// build in parallel.
 #include "kernels.h"
 
 #define SCION_CAT_(a, b) a##b
@@ -11,15 +12,14 @@ namespace scion {
 #if defined(SCION_OWN)
 #define SCION_FAMILY_OWN true
 #define SCION_W 2
-#define SCION_PREC 0
-#define SCION_GETTER kernels_own
+#define SCION_GETTER SCION_CAT(kernels_own_p, SCION_PREC)
 #else
 #define SCION_FAMILY_OWN false
 #define SCION_GETTER SCION_CAT(SCION_CAT(SCION_CAT(kernels_w, SCION_W), _p), SCION_PREC)
 #endif
 
 template <int SOA, int CREF, bool ANY, bool STATS>
-__global__ void __launch_bounds__(kMaxThreadsPerBlock) trace_kernel(TraceArgs a) {
+__global__ void __launch_bounds__(kMaxThreadsPerBlock, kMinBlocksPerSm) trace_kernel(TraceArgs a) {
   trace_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, ANY, STATS>(a);
 }
 

@@ -36,7 +36,7 @@ class ScionError(RuntimeError):
 class LayoutDesc(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "width", "box_layout", "box_prec", "child_ref", "prim_ref", "order", "leaf_max",
-        "sah_bins", "treelet_bytes", "reserved")]
+        "sah_bins", "treelet_bytes", "align")]
 
 
 class TraceParams(ctypes.Structure):
@@ -49,21 +49,21 @@ class DebugInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_uint32), ("node_stride", ctypes.c_uint32),
                 ("n_leaf_entries", ctypes.c_uint32), ("root_ref", ctypes.c_uint32),
                 ("depth", ctypes.c_uint32), ("stack_need", ctypes.c_uint32),
-                ("own_box", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("own_box", ctypes.c_uint32), ("node2_bytes", ctypes.c_uint32),
                 ("node_bytes", ctypes.c_uint64), ("prim_bytes", ctypes.c_uint64),
                 ("vert_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
 
 
-PREC = {"f32": 0, "f16": 1, "u8": 2}
+PREC = {"f32": 0, "f16": 1, "u8": 2, "q16": 3, "eq10": 4}
 ORDER = {"dfs": 0, "bfs": 1, "treelet": 2}
 
 
 def layout(width=2, box_layout="aos", box_prec="f32", child_ref="direct", prim_ref="indirect",
-           order="dfs", leaf_max=4, sah_bins=16, treelet_bytes=1024) -> LayoutDesc:
+           order="dfs", leaf_max=4, sah_bins=16, treelet_bytes=1024, align=0) -> LayoutDesc:
     """A layout descriptor from readable names."""
     return LayoutDesc(width, 0 if box_layout == "aos" else 1, PREC[box_prec],
                       0 if child_ref == "direct" else 1, 0 if prim_ref == "direct" else 1,
-                      ORDER[order], leaf_max, sah_bins, treelet_bytes, 0)
+                      ORDER[order], leaf_max, sah_bins, treelet_bytes, align)
 
 
 # The four node layouts swept on the coherent/incoherent workloads, each with
@@ -76,9 +76,22 @@ SWEEP = {
 }
 
 
-def sweep_layouts():
+# The world-grid quantised bvh2 layouts of Table 1 (Section 9.2.5, App. D.1,
+# D.3): sg-pbrt-q16, sg-pbrt-q16-soaos, sg-eq and sg-eq-align16.
+SWEEP_BVH2_QUANT = {
+    "bvh2_aos_q16": dict(width=2, box_layout="aos", box_prec="q16"),
+    "bvh2_soa_q16": dict(width=2, box_layout="soa", box_prec="q16"),
+    "bvh2_aos_eq10": dict(width=2, box_layout="aos", box_prec="eq10"),
+    "bvh2_aos_eq10_a16": dict(width=2, box_layout="aos", box_prec="eq10", align=16),
+}
+
+
+def sweep_layouts(quantised_bvh2: bool = False):
+    """Named descriptors of the swept layouts, each with direct and indirect
+    triangle storage (plus the quantised bvh2 layouts if asked)."""
     out = {}
-    for name, kw in SWEEP.items():
+    sweep = dict(SWEEP, **SWEEP_BVH2_QUANT) if quantised_bvh2 else SWEEP
+    for name, kw in sweep.items():
         for pr in ("direct", "indirect"):
             out[f"{name}_{pr}"] = layout(prim_ref=pr, **kw)
     return out
@@ -118,6 +131,7 @@ def lib():
         L.scion_debug_build_host.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), ctypes.POINTER(P)]
         L.scion_debug_host_stats.argtypes = [P, ctypes.POINTER(DebugInfo)]
         L.scion_debug_host_decode.argtypes = [P, P, P, P, P, P, P]
+        L.scion_debug_host_raw.argtypes = [P, P, U64, P, U64, P]
         L.scion_debug_host_destroy.argtypes = [P]
         L.scion_debug_host_destroy.restype = None
         L.scion_debug_f16_round.argtypes = [ctypes.c_float, I]
@@ -128,7 +142,7 @@ def lib():
                      "scion_trace_stats", "scion_trace_backward", "scion_batch_create",
                      "scion_batch_launch", "scion_batch_info", "scion_trace_batched",
                      "scion_get_status", "scion_debug_build_host", "scion_debug_host_stats",
-                     "scion_debug_host_decode"):
+                     "scion_debug_host_decode", "scion_debug_host_raw"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -498,6 +512,9 @@ class HostDecode:
     boxes: np.ndarray
     own_boxes: np.ndarray
     leaf_ids: np.ndarray
+    nodes: np.ndarray = None    # raw node array bytes
+    nodes2: np.ndarray = None   # raw second node array bytes (own-box SoA)
+    frame: np.ndarray = None    # world grid of the quantised own-box codecs
 
 
 def scion_debug_build_host(verts, desc: LayoutDesc, indices=None) -> HostDecode:
@@ -523,10 +540,17 @@ def scion_debug_build_host(verts, desc: LayoutDesc, indices=None) -> HostDecode:
         P = lambda x: x.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
         _check(lib().scion_debug_host_decode(h, P(kind), P(a), P(c), P(boxes), P(own), P(ids)),
                "scion_debug_host_decode")
+        n1 = inf.node_bytes - inf.node2_bytes
+        raw1 = np.zeros(max(n1, 1), np.uint8)
+        raw2 = np.zeros(max(inf.node2_bytes, 1), np.uint8)
+        frame = np.zeros(9, np.float32)
+        _check(lib().scion_debug_host_raw(h, P(raw1), n1, P(raw2), inf.node2_bytes, P(frame)),
+               "scion_debug_host_raw")
     finally:
         lib().scion_debug_host_destroy(h)
     return HostDecode(info, kind.reshape(nn, 8), a.reshape(nn, 8), c.reshape(nn, 8),
-                      boxes.reshape(nn, 8, 6), own.reshape(nn, 6), ids[:inf.n_leaf_entries])
+                      boxes.reshape(nn, 8, 6), own.reshape(nn, 6), ids[:inf.n_leaf_entries],
+                      raw1[:n1], raw2[:inf.node2_bytes], frame)
 
 
 def scion_debug_f16_round(x: float, direction: int) -> int:

@@ -1,11 +1,11 @@
 """GPU parity: every layout's closest-hit and any-hit results match the CPU
 oracle bit for bit (hit/miss, prim, t, u, v), through the C ABI."""
-import itertools
 import math
 
 import numpy as np
 import pytest
 
+from layout_cases import all_layouts
 from paper_2511_15028_gb300 import scenes
 
 torch = pytest.importorskip("torch")
@@ -44,13 +44,7 @@ def assert_same_hits(got, exp, what=""):
     assert bad.size == 0, f"{what}: {bad.size} mismatches, first {bad[:5]}: gpu {got[bad[:3]]} oracle {exp[bad[:3]]}"
 
 
-ALL = []
-for w, lay, prec, cref, pref, order in itertools.product(
-        (2, 4, 8), ("aos", "soa"), ("f32", "f16", "u8"), ("direct", "indirect"),
-        ("direct", "indirect"), ("dfs", "bfs", "treelet")):
-    if w == 2 and prec == "f32" and cref == "direct" and order != "dfs":
-        continue
-    ALL.append(dict(width=w, box_layout=lay, box_prec=prec, child_ref=cref, prim_ref=pref, order=order))
+ALL = all_layouts()
 
 
 @pytest.fixture(scope="module")
@@ -73,10 +67,13 @@ def test_config1_every_layout_bit_exact(sc_mod, config1, kw):
     unordered = gpu_closest(sc_mod, bvh, rays, params=dict(ordered_children=2))
     assert_same_hits(unordered, exp, "unordered")
     lane = gpu_closest(sc_mod, bvh, rays, params=dict(rays_per_fetch=1))
-    assert_same_hits(lane, exp, "per-lane fetch")
+    assert_same_hits(lane, exp, "refill 1")
+    lane = gpu_closest(sc_mod, bvh, rays, params=dict(rays_per_fetch=13))
+    assert_same_hits(lane, exp, "refill 13")
     nearest = gpu_closest(sc_mod, bvh, rays, params=dict(ordered_children=3))
     assert_same_hits(nearest, exp, "nearest first")
     assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(rays_per_fetch=1)), occ)
+    assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(rays_per_fetch=31)), occ)
     assert sc_mod.scion_get_status(bvh) == 0
 
 
@@ -168,6 +165,10 @@ def test_device_errors_are_reported_not_faulted(sc_mod):
     assert np.any(got["prim"] == 0xFFFFFFFE)
     assert sc_mod.scion_get_status(bvh) == 6
     assert sc_mod.scion_get_status(bvh) == 0  # cleared
+    got = gpu_closest(sc_mod, bvh, rays, params=dict(max_steps=1, rays_per_fetch=4))
+    assert np.any(got["prim"] == 0xFFFFFFFE) and sc_mod.scion_get_status(bvh) == 6
+    with pytest.raises(sc_mod.ScionError):
+        gpu_closest(sc_mod, bvh, rays, params=dict(rays_per_fetch=33))
     # a chain: triangles at x = 4^k (k = -50..49) whose two-bin SAH tree peels
     # one triangle per level (depth 100); a ray along +x through all of them
     # pushes one far child per level, more than the 64-entry stack holds
@@ -186,6 +187,8 @@ def test_device_errors_are_reported_not_faulted(sc_mod):
     got = gpu_closest(sc_mod, b, ray)
     assert got["prim"][0] == 0xFFFFFFFE
     assert sc_mod.scion_get_status(b) == 5
+    got = gpu_closest(sc_mod, b, ray, params=dict(rays_per_fetch=1))
+    assert got["prim"][0] == 0xFFFFFFFE and sc_mod.scion_get_status(b) == 5
     # a short ray that ends before the deep part is unaffected
     ok = gpu_any(sc_mod, b, np.array([[-1.0, 0.0, 0.0, 0.0, -1, 0, 0, np.inf]], np.float32))
     assert ok[0] == 0 and sc_mod.scion_get_status(b) == 0
@@ -193,7 +196,8 @@ def test_device_errors_are_reported_not_faulted(sc_mod):
 
 def test_config2_reduced_all_ray_kinds(sc_mod, oracle_mod):
     """Scaled-down coherent + incoherent workload (height field + spheres):
-    primary, one diffuse bounce, shadow rays; all eight swept layouts."""
+    primary, one diffuse bounce, shadow rays; the eight swept layouts and the
+    quantised bvh2 layouts."""
     sc = scenes.config2_scene(side=181, n_spheres=64)
     tris = sc.triangles()
     prim = scenes.config2_primary(320, 180)
@@ -203,7 +207,7 @@ def test_config2_reduced_all_ray_kinds(sc_mod, oracle_mod):
     shadow = scenes.shadow_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"])
     eb = ob.closest(bounce)
     es = ob.any(shadow)
-    for name, d in sc_mod.sweep_layouts().items():
+    for name, d in sc_mod.sweep_layouts(quantised_bvh2=True).items():
         bvh = sc_mod.scion_build(sc.verts, d, sc.indices)
         assert_same_hits(gpu_closest(sc_mod, bvh, prim), h, name + " primary")
         assert_same_hits(gpu_closest(sc_mod, bvh, bounce), eb, name + " bounce")
@@ -221,10 +225,11 @@ def test_random_soup_incoherent(sc_mod, oracle_mod):
     ob = oracle_mod.BVH2(tris)
     exp = ob.closest(rays)
     eocc = ob.any(short)
-    for name, d in sc_mod.sweep_layouts().items():
+    for name, d in sc_mod.sweep_layouts(quantised_bvh2=True).items():
         bvh = sc_mod.scion_build(verts, d)
         for p in (None, dict(rays_per_fetch=1), dict(rays_per_fetch=1, ordered_children=2, threads_per_block=128),
-                  dict(ordered_children=3), dict(rays_per_fetch=1, ordered_children=3)):
+                  dict(ordered_children=3), dict(rays_per_fetch=1, ordered_children=3), dict(rays_per_fetch=8),
+                  dict(rays_per_fetch=16, threads_per_block=64), dict(rays_per_fetch=32)):
             assert_same_hits(gpu_closest(sc_mod, bvh, rays, params=p), exp, name + " " + str(p))
             assert np.array_equal(gpu_any(sc_mod, bvh, short, params=p), eocc), name + " " + str(p)
 

@@ -3,12 +3,13 @@ back to the same leaves, every decoded box encloses its subtree (quantised
 bounds always enclose the original, Section 9.1 footnote; round-trip
 soundness, App. B), node sizes match Table 1 where the layouts coincide, and
 invalid descriptors are rejected."""
-import itertools
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
 
+from layout_cases import WORLD_GRID, all_layouts
 from paper_2511_15028_gb300 import scenes, scion
 
 
@@ -17,18 +18,6 @@ def _lib():
     from paper_2511_15028_gb300 import build as b
     b.build()
     scion.lib()
-
-
-def all_layouts():
-    out = []
-    for w, lay, prec, cref, pref, order in itertools.product(
-            (2, 4, 8), ("aos", "soa"), ("f32", "f16", "u8"), ("direct", "indirect"),
-            ("direct", "indirect"), ("dfs", "bfs", "treelet")):
-        own = w == 2 and prec == "f32"
-        if own and cref == "direct" and order != "dfs":
-            continue
-        out.append(dict(width=w, box_layout=lay, box_prec=prec, child_ref=cref, prim_ref=pref, order=order))
-    return out
 
 
 def walk(dec):
@@ -118,6 +107,14 @@ def test_pbrt_node_size_and_wide_sizes():
     for (w, p, c), size in expect.items():
         i = scion.scion_debug_build_host(sc.verts, scion.layout(width=w, box_prec=p, child_ref=c), sc.indices).info
         assert i["node_stride"] == size, (w, p, c)
+    # Table 1 bvh2 codecs: sg-pbrt-q16 16 B (also -soaos: 12 + 4), sg-eq 12 B,
+    # sg-eq-align16 16 B, pbrt-soaos-align16 32 + 8 B
+    for kw, per_node in ((dict(box_prec="q16"), 16), (dict(box_prec="q16", box_layout="soa"), 16),
+                         (dict(box_prec="eq10"), 12), (dict(box_prec="eq10", align=16), 16),
+                         (dict(box_prec="q16", box_layout="soa", align=16), 20),
+                         (dict(box_layout="soa", align=16), 40), (dict(align=16), 32)):
+        i = scion.scion_debug_build_host(sc.verts, scion.layout(**kw), sc.indices).info
+        assert i["own_box"] == 1 and i["node_bytes"] == per_node * i["n_nodes"], kw
 
 
 def test_soup_extreme_coordinates_enclosure():
@@ -128,12 +125,14 @@ def test_soup_extreme_coordinates_enclosure():
         v = scenes.random_soup(rng, 3000, mu=math.log(0.01)) * scale + offset
         v = v.astype(np.float32)
         tris = v.reshape(-1, 9)
-        for prec in ("f32", "f16", "u8"):
-            for w in (2, 4, 8):
+        for prec in ("f32", "f16", "u8") + WORLD_GRID:
+            for w in ((2,) if prec in WORLD_GRID else (2, 4, 8)):
                 dec = scion.scion_debug_build_host(v, scion.layout(width=w, box_prec=prec))
                 sub, leaves = walk(dec)
                 check_enclosure(dec, sub, tris)
                 assert sum(len(l) for l in leaves) == 3000
+                if prec in WORLD_GRID:
+                    check_world_grid(dec)
 
 
 def test_degenerate_scenes():
@@ -141,12 +140,15 @@ def test_degenerate_scenes():
     sc = scenes.config1_scene()
     flat = sc.verts.copy()
     flat[:, 2] = 0.5
-    for prec in ("f32", "f16", "u8"):
-        dec = scion.scion_debug_build_host(flat, scion.layout(width=8, box_prec=prec), sc.indices)
+    for w, prec in ((8, "f32"), (8, "f16"), (8, "u8"), (2, "q16"), (2, "eq10")):
+        dec = scion.scion_debug_build_host(flat, scion.layout(width=w, box_prec=prec), sc.indices)
         sub, _ = walk(dec)
         check_enclosure(dec, sub, flat[sc.indices].reshape(-1, 9))
+        if prec in WORLD_GRID:
+            check_world_grid(dec)
     one = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
-    for kw in ({}, dict(width=8, box_prec="u8"), dict(width=4, box_prec="f16", child_ref="indirect")):
+    for kw in ({}, dict(width=8, box_prec="u8"), dict(width=4, box_prec="f16", child_ref="indirect"),
+               dict(box_prec="q16"), dict(box_prec="eq10")):
         dec = scion.scion_debug_build_host(one, scion.layout(**kw))
         sub, leaves = walk(dec)
         assert leaves == [(0,)]
@@ -173,8 +175,10 @@ def test_nonfinite_triangles_left_out_and_empty_scene():
 
 def test_invalid_descriptors_rejected():
     v = scenes.config1_scene().triangles().reshape(-1, 3)
-    bad = [dict(width=3), dict(width=16), dict(box_prec=3), dict(order=3), dict(leaf_max=17),
-           dict(sah_bins=1), dict(sah_bins=65), dict(reserved=1),
+    bad = [dict(width=3), dict(width=16), dict(box_prec=5), dict(order=3), dict(leaf_max=17),
+           dict(sah_bins=1), dict(sah_bins=65), dict(align=1), dict(align=32),
+           dict(width=4, box_prec=3), dict(width=8, box_prec=4), dict(box_prec=3, leaf_max=16),
+           dict(box_prec=4, box_layout=1), dict(width=2, box_prec=3, child_ref=0, order=1),
            dict(width=2, box_prec=0, child_ref=0, order=1), dict(width=2, box_prec=0, child_ref=0, order=2)]
     for b in bad:
         d = scion.layout()
@@ -239,3 +243,133 @@ def test_f16_directed_rounding_against_numpy():
             nxt = np.nextafter(np.float16(lo), np.float16(np.inf)) if math.isfinite(lo) else None
             if nxt is not None and math.isfinite(hi):
                 assert float(nxt) == hi, (x, lo, hi, a)
+
+
+# ------------------------------------------------------------ world-grid codecs
+def _f32_round(fr, mode):
+    """Exact rounding of a rational to binary32: 'rn' (ties to even), 'rd'
+    (toward -inf) or 'ru' (toward +inf)."""
+    x = np.float32(float(fr))
+    cands = [np.nextafter(x, np.float32(-np.inf)), x, np.nextafter(x, np.float32(np.inf))]
+    cands = [c for c in cands if np.isfinite(c)]
+    if mode == "rd":
+        return max((c for c in cands if Fraction(float(c)) <= fr), key=float)
+    if mode == "ru":
+        return min((c for c in cands if Fraction(float(c)) >= fr), key=float)
+    best = min(abs(Fraction(float(c)) - fr) for c in cands)
+    near = [c for c in cands if abs(Fraction(float(c)) - fr) == best]
+    return near[0] if len(near) == 1 else [c for c in near if int(np.array(c).view(np.uint32)) % 2 == 0][0]
+
+
+def _world_grid_codes(dec):
+    """(lo codes [n,3], hi codes [n,3], words [n]) read from the raw bytes."""
+    d = dec.info
+    n, stride = d["n_nodes"], d["node_stride"]
+    raw = dec.nodes.reshape(n, stride)
+    if d["node2_bytes"]:  # q16 -soaos: code records + a word array
+        codes = raw[:, :12].copy().view("<u2").reshape(n, 6).astype(np.int64)
+        return codes[:, :3], codes[:, 3:], dec.nodes2.view("<u4").copy()
+    if stride == 16 and dec.frame[6] == 0.0:  # q16 AoS: 6 codes + word
+        codes = raw[:, :12].copy().view("<u2").reshape(n, 6).astype(np.int64)
+        return codes[:, :3], codes[:, 3:], raw[:, 12:16].copy().view("<u4").ravel()
+    w = raw[:, :12].copy().view("<u4").reshape(n, 3)  # eq10: lo word, hi word, node word
+    unpack = lambda x: np.stack([(x >> 20) & 1023, (x >> 10) & 1023, x & 1023], 1).astype(np.int64)  # noqa: E731
+    return unpack(w[:, 0]), unpack(w[:, 1]), w[:, 2]
+
+
+def check_world_grid(dec, limit=None):
+    """Decode every node's box from its codes with exact rational arithmetic
+    (q16: coordinate = RN(code * step + wlo); eq10, the App. D.1 grid with
+    one outward rounding: lo = RD(code * bin + wlo), hi = RU(whi - code * bin))
+    and compare
+    with the packer's decode bit for bit; the node word's count and child
+    fields must match the decoded tree."""
+    n = dec.info["n_nodes"]
+    if n == 0:
+        return
+    lo_c, hi_c, words = _world_grid_codes(dec)
+    f = [Fraction(float(x)) for x in dec.frame]
+    eq = dec.frame[6] != 0.0  # eq10 bins are never 0; q16 leaves these slots 0
+    idx = range(n) if limit is None else np.random.default_rng(0).choice(n, min(n, limit), replace=False)
+    for x in idx:
+        for a in range(3):
+            if eq:
+                lo = _f32_round(f[a] + lo_c[x, a] * f[6 + a], "rd")
+                hi = _f32_round(f[3 + a] - hi_c[x, a] * f[6 + a], "ru")
+                assert 0 <= lo_c[x, a] <= 1023 and 0 <= hi_c[x, a] <= 1023
+            else:
+                lo = _f32_round(lo_c[x, a] * f[3 + a] + f[a], "rn")
+                hi = _f32_round(hi_c[x, a] * f[3 + a] + f[a], "rn")
+            got_lo, got_hi = dec.own_boxes[x, a], dec.own_boxes[x, 3 + a]
+            assert np.array([lo], np.float32).view(np.uint32)[0] == np.array([got_lo], np.float32).view(np.uint32)[0]
+            assert np.array([hi], np.float32).view(np.uint32)[0] == np.array([got_hi], np.float32).view(np.uint32)[0]
+        w = int(words[x])
+        cnt = w & 15
+        if cnt:
+            assert dec.kind[x, 0] == 2 and dec.c[x, 0] == cnt and dec.a[x, 0] == w >> 4
+        else:
+            assert dec.kind[x, 0] == 1 and dec.kind[x, 1] == 1 and (w >> 4) & 3 <= 2
+
+
+@pytest.mark.parametrize("kw", [dict(box_prec="q16"), dict(box_prec="q16", box_layout="soa"),
+                                dict(box_prec="q16", box_layout="soa", align=16),
+                                dict(box_prec="eq10"), dict(box_prec="eq10", align=16),
+                                dict(box_prec="q16", child_ref="indirect", order="bfs")],
+                         ids=lambda kw: "-".join(str(v) for v in kw.values()))
+def test_world_grid_codecs_decode_independently(kw):
+    sc = scenes.config1_scene()
+    dec = scion.scion_debug_build_host(sc.verts, scion.layout(**kw), sc.indices)
+    check_world_grid(dec)
+    sub, _ = walk(dec)
+    check_enclosure(dec, sub, sc.triangles())
+
+
+def test_world_grid_frames_and_slack():
+    """The grid spans the root box; eq10's bins follow App. D.1
+    (bins_inv = RD(1023 / RU(whi - wlo)), bin = RD(1 / bins_inv)); q16's step is
+    the smallest float with RN(65535 * step + wlo) >= whi. Every decoded box
+    is at most about one grid step (plus the build pad) looser than its
+    subtree's bounds."""
+    sc = scenes.config2_scene(side=65, n_spheres=16)
+    tris = sc.triangles()
+    P = tris.reshape(-1, 3, 3)
+    for prec in WORLD_GRID:
+        dec = scion.scion_debug_build_host(sc.verts, scion.layout(box_prec=prec), sc.indices)
+        sub, _ = walk(dec)
+        fr = dec.frame
+        root_lo, root_hi = dec.own_boxes[0, :3], dec.own_boxes[0, 3:]
+        for a in range(3):
+            wlo = Fraction(float(fr[a]))
+            if prec == "eq10":
+                whi = Fraction(float(fr[3 + a]))
+                L = _f32_round(whi - wlo, "ru")
+                L = L if L > 0 else np.float32(1.0)
+                inv = _f32_round(Fraction(1023) / Fraction(float(L)), "rd")
+                assert fr[6 + a] == _f32_round(1 / Fraction(float(inv)), "rd")
+                step = float(fr[6 + a])
+                assert root_lo[a] <= fr[a] and root_hi[a] >= fr[3 + a]
+            else:
+                step = float(fr[3 + a])
+                top = _f32_round(65535 * Fraction(step) + wlo, "rn")
+                below = _f32_round(65535 * Fraction(float(np.nextafter(np.float32(step), np.float32(0)))) + wlo, "rn")
+                assert root_lo[a] == fr[a] and top >= root_hi[a] and below < root_hi[a]
+        for x, ids in sub.items():
+            q = P[ids].reshape(-1, 3)
+            tlo, thi = q.min(0).astype(np.float64), q.max(0).astype(np.float64)
+            ext = float(np.max(thi - tlo))
+            mag = float(np.max(np.abs(np.concatenate([tlo, thi]))))
+            pad = 2.0 ** -19 * (ext + mag) + 1e-30
+            steps = fr[6:9] if prec == "eq10" else fr[3:6]
+            assert np.all(tlo - dec.own_boxes[x, :3] <= 2 * steps + pad), (prec, x)
+            assert np.all(dec.own_boxes[x, 3:] - thi <= 2 * steps + pad), (prec, x)
+
+
+def test_world_grid_limits():
+    """leaf_max above the 4-bit count field and layouts outside the codec's
+    forms are rejected; a scene of one point builds (zero-extent grid)."""
+    pt = np.zeros((30, 3), np.float32) + np.float32(-7.5)
+    for prec in WORLD_GRID:
+        dec = scion.scion_debug_build_host(pt, scion.layout(box_prec=prec, leaf_max=15))
+        _, leaves = walk(dec)
+        assert sum(len(l) for l in leaves) == 10
+        check_world_grid(dec)
