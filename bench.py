@@ -416,6 +416,78 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
             "pareto_any": pareto({k: (v["bvh_mb"], v["any"]["mrays_s"]) for k, v in out.items()})}
 
 
+def time_query(scion, torch, bvh, fn, rays, out, steps, warmup):
+    """Trimmed-mean ms of one query in its measured-fastest traversal mode."""
+    mode, trials = pick_fetch(scion, torch, bvh, fn, rays, out, reps=2)
+    p = FETCH_MODES[mode] or None
+    for _ in range(warmup):
+        fn(bvh, rays, out, params=p)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn(bvh, rays, out, params=p)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return trimmed_mean(ts), mode
+
+
+# ------------------------------------------------------------------ GPU construction
+def bench_build(scion, torch, steps, warmup):
+    """Logical-BVH2 construction on the host (binned SAH, all host cores) and
+    on the GPU (linear BVH), both packed by the same host packers; and the
+    incoherent workload traced on both kinds of tree."""
+    from paper_2511_15028_gb300 import scenes
+    tiny = torch.tensor([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=torch.float32, device="cuda")
+    scion.scion_build_gpu(tiny, scion.layout())  # first-call costs out of the timings
+    out = {}
+    sc2 = scenes.config2_scene()
+    sc3 = scenes.config3_scene()
+    for name, sc, ix in (("coherent_1373138_tris", sc2, sc2.indices), ("incoherent_8388608_tris", sc3, None)):
+        dv = torch.from_numpy(sc.verts).cuda()
+        dix = None if ix is None else torch.from_numpy(ix.astype(np.int32)).cuda()
+        res = {"tris": sc.n_tris}
+        lays = {"bvh4_soa_f32_direct": scion.layout(width=4, box_layout="soa", prim_ref="direct"),
+                "bvh8_aos_u8_direct": scion.layout(width=8, box_prec="u8", prim_ref="direct")}
+        trees = {}
+        for builder in ("sah_host", "lbvh_gpu"):
+            for lname, desc in lays.items():
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                bvh = (scion.scion_build(sc.verts, desc, ix) if builder == "sah_host"
+                       else scion.scion_build_gpu(dv, desc, dix))
+                wall = (time.perf_counter() - t0) * 1e3
+                bt = scion.scion_bvh_build_times(bvh)
+                info = scion.scion_bvh_info(bvh)
+                res.setdefault(builder, {})[lname] = {
+                    "logical_ms": round(bt["logical_ms"], 2), "pack_ms": round(bt["pack_ms"], 2),
+                    "wall_ms": round(wall, 1), "n_nodes": info["n_nodes"], "depth": info["depth"],
+                    "bvh_mb": (info["node_bytes"] + info["prim_bytes"]) / 1e6}
+                trees[(builder, lname)] = bvh
+        res["lbvh_logical_mtris_s"] = sc.n_tris / (res["lbvh_gpu"]["bvh4_soa_f32_direct"]["logical_ms"] / 1e3) / 1e6
+        res["sah_logical_mtris_s"] = sc.n_tris / (res["sah_host"]["bvh4_soa_f32_direct"]["logical_ms"] / 1e3) / 1e6
+        if sc is sc3:
+            rays = torch.from_numpy(scenes.config3_rays()).cuda()
+            short = rays.clone()
+            short[:, 7] = 0.05
+            n = rays.shape[0]
+            hits = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+            occ = torch.empty((n,), dtype=torch.int32, device="cuda")
+            tr = {}
+            for (builder, lname), bvh in trees.items():
+                mc, fc = time_query(scion, torch, bvh, scion.scion_trace_closest, rays, hits, steps, warmup)
+                ma, fa = time_query(scion, torch, bvh, scion.scion_trace_any, short, occ, steps, warmup)
+                tr[f"{builder}/{lname}"] = {"closest_mrays_s": n / (mc / 1e3) / 1e6, "closest_mode": fc,
+                                            "any_mrays_s": n / (ma / 1e3) / 1e6, "any_mode": fa}
+            res["trace"] = tr
+        for bvh in trees.values():
+            scion.scion_destroy(bvh)
+        out[name] = res
+    return out
+
+
 # ------------------------------------------------------------------ batched (config 4)
 def bench_batched(scion, torch, steps, warmup, flush_buf, seed=1004):
     """64 uneven scenes, each with its own rays and autotuned layout: one
@@ -541,8 +613,9 @@ def main():
     ap.add_argument("--layouts", default="all", help="all | comma-separated sweep names")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the incoherent, batched and backward measurements")
-    ap.add_argument("--section", default="all", choices=["all", "incoherent"],
-                    help="incoherent: only the 2^23-triangle section (for profiling)")
+    ap.add_argument("--section", default="all", choices=["all", "incoherent", "build"],
+                    help="incoherent: only the 2^23-triangle section (for profiling); "
+                         "build: only the host/GPU construction section")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -567,6 +640,12 @@ def main():
     from paper_2511_15028_gb300 import build as native_build
     native_build.build()
     from paper_2511_15028_gb300 import scion
+
+    if args.section == "build":
+        res = bench_build(scion, torch, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"section": "build", "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
+        return
 
     if args.section == "incoherent":
         pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -675,6 +754,7 @@ def main():
         extra["incoherent"] = bench_incoherent(scion, torch, args.steps, args.warmup, hbm_peak)
         extra["batched"] = bench_batched(scion, torch, args.steps, args.warmup, flush_buf)
         extra["backward"] = bench_backward(scion, torch, args.steps, args.warmup)
+        extra["build"] = bench_build(scion, torch, args.steps, args.warmup)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

@@ -167,6 +167,30 @@ scion_status scion_build_many(const float *verts, uint64_t n_verts, const uint32
                               uint64_t n_tris, const scion_layout_desc *descs, uint32_t n_desc,
                               scion_stream stream, scion_bvh *out);
 
+/* The same as scion_build, but the logical BVH2 is constructed on the GPU
+ * (Section 5.1 keeps construction apart from the layout build; Section 2:
+ * topology is orthogonal to layout) as a linear BVH: 30-bit Morton codes of
+ * the triangle centroids, a stable radix sort, the binary radix tree of
+ * Karras (2012) and boxes bottom-up; one triangle per leaf (leaf_max and
+ * sah_bins are not used). The tree is then packed into `desc` by the same
+ * host packers as scion_build.
+ *  d_verts   : float [n_verts][3], DEVICE memory (read, not retained).
+ *  d_indices : uint32 [n_tris][3] in DEVICE memory, or NULL for a soup.
+ *  stream    : stream for the build kernels and copies; the call returns
+ *              after they complete.
+ * Device scratch of about 60 bytes per triangle is allocated for the
+ * duration of the call. Errors as scion_build; host pointers give
+ * INVALID_ARG. */
+scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices,
+                             uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
+                             scion_bvh *out);
+
+/* Build timings of a BVH in milliseconds: logical_ms = construction of the
+ * logical BVH2 (host wall time of the binned-SAH builder, or device time of
+ * scion_build_gpu's kernels); pack_ms = host packing into the layout. Either
+ * pointer may be NULL. */
+scion_status scion_bvh_build_times(scion_bvh bvh, double *logical_ms, double *pack_ms);
+
 /* Sizes of the device buffers (bytes) and tree shape. Any output pointer may
  * be NULL. node_bytes: node buffer(s); prim_bytes: leaf primitive buffer
  * (direct triangles, or ids plus the index table for indirect); depth: levels

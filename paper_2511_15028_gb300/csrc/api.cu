@@ -15,6 +15,7 @@
 #include "batched.h"
 #include "builder.h"
 #include "kernels.h"
+#include "lbvh.h"
 
 using namespace scion;
 
@@ -40,7 +41,7 @@ struct scion_bvh_s {
   std::mutex slot_mu;
   uint32_t n_slots = 0;
   cudaStream_t slot_stream[kStreamSlotCount] = {};
-  double build_ms = 0.0;
+  double build_ms = 0.0, logical_ms = 0.0, pack_ms = 0.0;
   int device = 0;
 };
 
@@ -185,8 +186,10 @@ scion_status build_host_many(const float *v, uint64_t n_verts, const uint32_t *i
         g_last_error = err;
         return st;
       }
-      (*hbs)[i].build_ms =
-          logical_ms + std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+      HostBVH &h = (*hbs)[i];
+      h.logical_ms = logical_ms;
+      h.pack_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+      h.build_ms = h.logical_ms + h.pack_ms;
     }
   } catch (const std::bad_alloc &) {
     g_last_error = "out of host memory";
@@ -213,12 +216,15 @@ scion_status build_host(const float *v, uint64_t n_verts, const uint32_t *ix, ui
   try {
     LogicalBVH lb;
     build_logical(in, d.sah_bins, d.leaf_max, &lb);
+    const auto t1 = std::chrono::steady_clock::now();
+    hb->logical_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     std::string err;
     st = pack_bvh(in, lb, d, own_box, hb, &err);
     if (st != SCION_OK) {
       g_last_error = err;
       return st;
     }
+    hb->pack_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
   } catch (const std::bad_alloc &) {
     g_last_error = "out of host memory";
     return SCION_ERR_OOM;
@@ -321,6 +327,8 @@ scion_status upload_bvh(HostBVH &hb, uint64_t n_tris, uint64_t n_verts, bool ind
   b->stack_need = hb.stack_need;
   for (int k = 0; k < 9; ++k) b->frame[k] = hb.frame[k];
   b->build_ms = hb.build_ms;
+  b->logical_ms = hb.logical_ms;
+  b->pack_ms = hb.pack_ms;
   cudaGetDevice(&b->device);
   uint64_t pb = 0, pi = 0;
   scion_status us = SCION_OK;
@@ -403,6 +411,68 @@ scion_status scion_build(const float *verts, uint64_t n_verts, const uint32_t *i
   st = build_host(v, n_verts, ix, n_tris, desc, &hb);
   if (st != SCION_OK) return st;
   return upload_bvh(hb, n_tris, n_verts, ix != nullptr, s, out);
+}
+
+scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices,
+                             uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
+                             scion_bvh *out) {
+  if (!out) return SCION_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc || (n_tris > 0 && !d_verts)) return SCION_ERR_INVALID_ARG;
+  if (n_tris >= kMaxPrims || n_verts >= (1ull << 32)) return SCION_ERR_INVALID_ARG;
+  if (!d_indices && n_verts != 3 * n_tris) return SCION_ERR_INVALID_ARG;
+  if (n_tris > 0 && (!is_device_ptr(d_verts) || (d_indices && !is_device_ptr(d_indices)))) {
+    g_last_error = "scion_build_gpu: vertices and indices must be device memory";
+    return SCION_ERR_INVALID_ARG;
+  }
+  scion_layout_desc d;
+  bool own_box = false;
+  scion_status st = normalize_desc(*desc, &d, &own_box);
+  if (st != SCION_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  HostBVH hb;
+  try {
+    // host copies for the packers (direct triangles, vertex tables) and the
+    // index check, which must pass before any kernel reads through the indices
+    std::vector<float> hv;
+    std::vector<uint32_t> hi;
+    const float *v;
+    const uint32_t *ix;
+    st = host_inputs(d_verts, n_verts, d_indices, n_tris, s, &hv, &hi, &v, &ix);
+    if (st != SCION_OK) return st;
+    if (ix)
+      for (uint64_t i = 0; i < 3 * n_tris; ++i)
+        if (ix[i] >= n_verts) return SCION_ERR_INVALID_ARG;
+    LogicalBVH lb;
+    double gpu_ms = 0.0;
+    std::string err;
+    st = lbvh_build(d_verts, n_verts, d_indices, n_tris, s, &lb, &gpu_ms, &err);
+    if (st != SCION_OK) {
+      g_last_error = err;
+      return st;
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    st = pack_bvh(BuildInput{v, n_verts, ix, n_tris}, lb, d, own_box, &hb, &err);
+    if (st != SCION_OK) {
+      g_last_error = err;
+      return st;
+    }
+    hb.logical_ms = gpu_ms;
+    hb.pack_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+  } catch (const std::bad_alloc &) {
+    g_last_error = "out of host memory";
+    return SCION_ERR_OOM;
+  }
+  hb.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return upload_bvh(hb, n_tris, n_verts, d_indices != nullptr, s, out);
+}
+
+scion_status scion_bvh_build_times(scion_bvh bvh, double *logical_ms, double *pack_ms) {
+  if (!bvh) return SCION_ERR_INVALID_ARG;
+  if (logical_ms) *logical_ms = bvh->logical_ms;
+  if (pack_ms) *pack_ms = bvh->pack_ms;
+  return SCION_OK;
 }
 
 scion_status scion_build_many(const float *verts, uint64_t n_verts, const uint32_t *indices,

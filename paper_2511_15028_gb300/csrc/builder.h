@@ -59,7 +59,9 @@ struct HostBVH {
   uint32_t depth = 0;               // levels of the stored tree
   uint32_t stack_need = 0;          // worst-case traversal stack entries
   float frame[9] = {};              // world grid: q16 {wlo, step}, eq10 {wlo, whi, bin}
-  double build_ms = 0.0;
+  double build_ms = 0.0;             // whole host build (logical + pack)
+  double logical_ms = 0.0;           // logical BVH2 construction (host wall or GPU device time)
+  double pack_ms = 0.0;              // packing into the layout
 };
 
 struct BuildInput {

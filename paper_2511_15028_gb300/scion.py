@@ -110,6 +110,8 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         L.scion_build.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), P, ctypes.POINTER(P)]
+        L.scion_build_gpu.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), P, ctypes.POINTER(P)]
+        L.scion_bvh_build_times.argtypes = [P, P, P]
         L.scion_bvh_info.argtypes = [P, P, P, P, P]
         L.scion_build_many.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), U32, P, ctypes.POINTER(P)]
         L.scion_trace_closest.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
@@ -138,7 +140,8 @@ def lib():
         L.scion_debug_f16_round.restype = U32
         L.scion_debug_f16_decode.argtypes = [U32]
         L.scion_debug_f16_decode.restype = ctypes.c_float
-        for name in ("scion_build", "scion_build_many", "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
+        for name in ("scion_build", "scion_build_gpu", "scion_bvh_build_times", "scion_build_many",
+                     "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
                      "scion_trace_stats", "scion_trace_backward", "scion_batch_create",
                      "scion_batch_launch", "scion_batch_info", "scion_trace_batched",
                      "scion_get_status", "scion_debug_build_host", "scion_debug_host_stats",
@@ -213,6 +216,37 @@ def scion_build(verts, desc: LayoutDesc, indices=None, stream=None) -> BVH:
     _check(lib().scion_build(vp, nv, ip, nt, ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(h)),
            "scion_build")
     return BVH(h, nt, nv, desc)
+
+
+def scion_build_gpu(verts, desc: LayoutDesc, indices=None, stream=None) -> BVH:
+    """Build with the logical BVH2 constructed on the GPU (linear BVH, one
+    triangle per leaf), then packed into `desc`. verts: float32 [n_verts, 3]
+    and indices: int32/uint32 [n_tris, 3] (or None for a soup), CUDA tensors
+    or numpy arrays (copied to the device first)."""
+    import torch
+    v = torch.as_tensor(verts, dtype=torch.float32).cuda().contiguous()
+    ix = None
+    if indices is not None:
+        if isinstance(indices, torch.Tensor):
+            ix = indices.to(torch.int32)  # same bits as uint32 below 2^31
+        else:
+            ix = torch.from_numpy(_as_np(indices, np.uint32).view(np.int32))
+        ix = ix.cuda().contiguous()
+    nv = v.shape[0]
+    nt = nv // 3 if ix is None else ix.shape[0]
+    h = ctypes.c_void_p()
+    _check(lib().scion_build_gpu(ctypes.c_void_p(v.data_ptr()), nv,
+                                 None if ix is None else ctypes.c_void_p(ix.data_ptr()), nt,
+                                 ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(h)), "scion_build_gpu")
+    return BVH(h, nt, nv, desc)
+
+
+def scion_bvh_build_times(bvh: BVH) -> dict:
+    """{'logical_ms', 'pack_ms'}: logical BVH2 construction (host SAH wall
+    time or GPU build device time) and host packing."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().scion_bvh_build_times(bvh.handle, ctypes.byref(a), ctypes.byref(b)), "scion_bvh_build_times")
+    return {"logical_ms": a.value, "pack_ms": b.value}
 
 
 def scion_build_many(verts, descs, indices=None, stream=None):

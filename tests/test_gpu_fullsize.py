@@ -76,3 +76,28 @@ def test_config3_full_size(sc_mod, oracle_mod):
         assert np.array_equal(occ, eocc), name + " any"
         assert scion.scion_get_status(bvh) == 0
         del bvh
+
+
+def test_config3_full_size_gpu_built(sc_mod, oracle_mod):
+    """The 2^23-triangle soup with its logical BVH2 built on the GPU (linear
+    BVH), packed as BVH8 u8 and BVH4: 256 sampled rays against brute force."""
+    scion = sc_mod
+    sc = scenes.config3_scene()
+    rays = scenes.config3_rays()
+    short = rays.copy()
+    short[:, 7] = 0.05
+    pick = np.sort(np.random.default_rng(6).choice(rays.shape[0], 256, replace=False))
+    tris = sc.verts.reshape(-1, 9)
+    exp = oracle_mod.closest_brute(tris, rays[pick])
+    eocc = oracle_mod.any_brute(tris, short[pick])
+    d, ds = torch.from_numpy(rays).cuda(), torch.from_numpy(short).cuda()
+    dv = torch.from_numpy(sc.verts).cuda()
+    for desc in (scion.layout(width=8, box_prec="u8", prim_ref="direct"),
+                 scion.layout(width=4, box_layout="soa", prim_ref="direct")):
+        bvh = scion.scion_build_gpu(dv, desc)
+        got = scion.scion_trace_closest(bvh, d)[torch.from_numpy(pick).cuda()]
+        _cmp(scion, got, exp, "gpu-built closest")
+        occ = scion.scion_trace_any(bvh, ds).cpu().numpy().astype(np.uint32)[pick]
+        assert np.array_equal(occ, eocc)
+        assert scion.scion_get_status(bvh) == 0
+        del bvh
