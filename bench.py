@@ -481,7 +481,27 @@ def bench_build(scion, torch, steps, warmup):
                 ma, fa = time_query(scion, torch, bvh, scion.scion_trace_any, short, occ, steps, warmup)
                 tr[f"{builder}/{lname}"] = {"closest_mrays_s": n / (mc / 1e3) / 1e6, "closest_mode": fc,
                                             "any_mrays_s": n / (ma / 1e3) / 1e6, "any_mode": fa}
+            # refit the SAH trees to a slightly moved soup (every vertex moves by
+            # up to 1e-3, about half a triangle edge), then trace the moved scene
+            moved = dv + 1e-3 * torch.sin(dv * 37.0 + torch.arange(3, device="cuda"))
+            refit = {}
+            for lname in lays:
+                bvh = trees[("sah_host", lname)]
+                scion.scion_refit(bvh, moved)  # first call allocates the scratch
+                ts = []
+                for k in range(steps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    scion.scion_refit(bvh, dv if k % 2 == 0 else moved)
+                    b.record()
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                scion.scion_refit(bvh, moved)
+                mc, fc = time_query(scion, torch, bvh, scion.scion_trace_closest, rays, hits, steps, warmup)
+                refit[lname] = {"refit_ms": trimmed_mean(ts), "closest_mrays_s_after": n / (mc / 1e3) / 1e6,
+                                "closest_mode": fc}
             res["trace"] = tr
+            res["refit_sah_trees"] = refit
         for bvh in trees.values():
             scion.scion_destroy(bvh)
         out[name] = res

@@ -185,6 +185,26 @@ scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint3
                              uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
                              scion_bvh *out);
 
+/* Refit to new vertex positions: same triangles, same indices, same tree.
+ * Every node's box is recomputed bottom-up from the new vertices and
+ * re-encoded in place in the BVH's layout (the same codecs as the build,
+ * rounded outward, with the build pad), and the BVH's vertex table and
+ * direct triangle copies are rewritten. Results of later traces are those of
+ * the moved scene; tree quality degrades as the motion grows (rebuild then).
+ * Triangles left out at build time (non-finite) stay out; a triangle whose
+ * vertex becomes non-finite is never hit.
+ *  d_verts : float [n_verts][3], DEVICE memory; n_verts must equal the
+ *            BVH's vertex count.
+ *  stream  : the refit kernels run on it, asynchronously, except for the
+ *            world-grid layouts (q16, eq10), whose new grid is read back
+ *            (the call then synchronises the stream).
+ * No trace of this BVH may run concurrently on another stream. The first
+ * call allocates about 32 bytes of device scratch per node, kept until
+ * scion_destroy. A box code that cannot enclose its box sets the device
+ * status word to SCION_ERR_BAD_INPUT (scion_get_status).
+ * Errors: INVALID_ARG (null, host memory, vertex count), OOM, CUDA. */
+scion_status scion_refit(scion_bvh bvh, const float *d_verts, uint64_t n_verts, scion_stream stream);
+
 /* Build timings of a BVH in milliseconds: logical_ms = construction of the
  * logical BVH2 (host wall time of the binned-SAH builder, or device time of
  * scion_build_gpu's kernels); pack_ms = host packing into the layout. Either

@@ -16,6 +16,7 @@
 #include "builder.h"
 #include "kernels.h"
 #include "lbvh.h"
+#include "refit.h"
 
 using namespace scion;
 
@@ -43,6 +44,10 @@ struct scion_bvh_s {
   cudaStream_t slot_stream[kStreamSlotCount] = {};
   double build_ms = 0.0, logical_ms = 0.0, pack_ms = 0.0;
   int device = 0;
+  // refit scratch, allocated by the first scion_refit
+  uint32_t *d_refit_parent = nullptr, *d_refit_pending = nullptr;
+  void *d_refit_boxes = nullptr;
+  float *d_refit_frame = nullptr;
 };
 
 namespace {
@@ -83,7 +88,9 @@ scion_status cuda_fail(cudaError_t e) {
 
 void free_bvh(scion_bvh b) {
   if (!b) return;
-  void *bufs[] = {b->d_nodes, b->d_nodes2, b->d_prims, b->d_prim_ids, b->d_verts, b->d_idx, b->d_scratch};
+  void *bufs[] = {b->d_nodes,       b->d_nodes2,         b->d_prims,          b->d_prim_ids,
+                  b->d_verts,       b->d_idx,            b->d_scratch,        b->d_refit_parent,
+                  b->d_refit_pending, b->d_refit_boxes,  b->d_refit_frame};
   for (void *p : bufs)
     if (p) cudaFree(p);
   delete b;
@@ -466,6 +473,58 @@ scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint3
   }
   hb.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return upload_bvh(hb, n_tris, n_verts, d_indices != nullptr, s, out);
+}
+
+scion_status scion_refit(scion_bvh bvh, const float *d_verts, uint64_t n_verts, scion_stream stream) {
+  if (!bvh || n_verts != bvh->n_verts || (n_verts > 0 && !d_verts)) return SCION_ERR_INVALID_ARG;
+  if (n_verts > 0 && !is_device_ptr(d_verts)) {
+    g_last_error = "scion_refit: vertices must be device memory";
+    return SCION_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  scion_bvh b = bvh;
+  if (!b->d_refit_parent && b->n_nodes > 0) {
+    const size_t n = b->n_nodes;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_refit_parent), n * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_refit_pending), n * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_refit_boxes, n * 6 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_refit_frame), 16 * sizeof(float));
+    if (e != cudaSuccess) {
+      cudaFree(b->d_refit_parent);
+      cudaFree(b->d_refit_pending);
+      cudaFree(b->d_refit_boxes);
+      cudaFree(b->d_refit_frame);
+      b->d_refit_parent = b->d_refit_pending = nullptr;
+      b->d_refit_boxes = nullptr;
+      b->d_refit_frame = nullptr;
+      return e == cudaErrorMemoryAllocation ? SCION_ERR_OOM : cuda_fail(e);
+    }
+  }
+  RefitBuffers rb;
+  rb.nodes = b->d_nodes;
+  rb.nodes2 = b->d_nodes2;
+  rb.prims = b->d_prims;
+  rb.verts4 = b->d_verts;
+  rb.prim_ids = static_cast<const uint32_t *>(b->d_prim_ids);
+  rb.tri_idx = static_cast<const uint32_t *>(b->d_idx);
+  rb.n_nodes = b->n_nodes;
+  rb.node_stride = b->node_stride;
+  rb.n_leaf_entries = b->n_leaf_entries;
+  rb.n_verts = b->n_verts;
+  rb.own_box = b->own_box;
+  rb.desc = b->desc;
+  rb.parent = b->d_refit_parent;
+  rb.pending = b->d_refit_pending;
+  rb.boxes = b->d_refit_boxes;
+  rb.frame = b->d_refit_frame;
+  rb.status = b->d_scratch + 3;
+  SCION_CUDA(refit_launch(rb, d_verts, s));
+  if (prec_is_world_grid(b->desc.box_prec) && b->n_nodes > 0) {
+    // the traversal takes the grid as a launch argument: read it back
+    SCION_CUDA(cudaMemcpyAsync(b->frame, b->d_refit_frame, 9 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    SCION_CUDA(cudaStreamSynchronize(s));
+  }
+  return SCION_OK;
 }
 
 scion_status scion_bvh_build_times(scion_bvh bvh, double *logical_ms, double *pack_ms) {

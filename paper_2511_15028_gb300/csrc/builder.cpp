@@ -15,157 +15,6 @@
 
 namespace scion {
 
-// ------------------------------------------------------------ rounding helpers
-float round_down_f32(double x) {
-  float f = (float)x;
-  if ((double)f > x) f = std::nextafter(f, -INFINITY);
-  return f;
-}
-float round_up_f32(double x) {
-  float f = (float)x;
-  if ((double)f < x) f = std::nextafter(f, INFINITY);
-  return f;
-}
-
-float f16_to_f32(uint16_t h) {
-  uint32_t s = h >> 15, e = (h >> 10) & 31u, m = h & 1023u;
-  double v;
-  if (e == 0) v = std::ldexp((double)m, -24);
-  else if (e == 31) v = m ? NAN : INFINITY;
-  else v = std::ldexp((double)(1024u + m), (int)e - 25);
-  return (float)(s ? -v : v);
-}
-
-// IEEE binary16 with directed rounding: dir < 0 toward -inf, dir > 0 toward +inf.
-static uint16_t f16_directed(double x, int dir) {
-  if (std::isnan(x)) return 0x7E00;
-  if (x == 0.0) return std::signbit(x) ? 0x8000 : 0;
-  const bool neg = x < 0.0;
-  const double a = std::fabs(x);
-  uint16_t mag;  // largest finite f16 magnitude <= a
-  if (a >= 65504.0) {
-    mag = 0x7BFF;
-  } else {
-    int e;
-    std::frexp(a, &e);  // a = f * 2^e, f in [0.5, 1)
-    int E = e + 14;     // biased exponent of a normal f16 in [2^(E-15), 2^(E-14))
-    if (E >= 1) {
-      double f = std::floor((std::ldexp(a, 15 - E) - 1.0) * 1024.0);
-      mag = (uint16_t)((E << 10) | (int)f);
-    } else {
-      mag = (uint16_t)std::floor(std::ldexp(a, 24));
-    }
-  }
-  const bool exact = (double)f16_to_f32(mag) == a;
-  const bool away = (dir > 0 && !neg) || (dir < 0 && neg);
-  if (!exact && away) mag = (uint16_t)(mag + 1u);  // 0x7BFF + 1 = +inf pattern
-  return (uint16_t)((neg ? 0x8000u : 0u) | mag);
-}
-uint16_t f32_to_f16_down(float x) { return f16_directed(x, -1); }
-uint16_t f32_to_f16_up(float x) { return f16_directed(x, +1); }
-
-// Directed rounding of the exact value s + e to float (e is the error term
-// of an error-free transform, at most half an ulp of s): the nearest float to
-// s is at most one step away from the wanted one, and the comparison with
-// s + e decides the step exactly.
-static float round_dir(double s, double e, int dir) {
-  float f = (float)s;
-  if (std::isnan(f)) return f;
-  const bool above = (double)f > s || ((double)f == s && e < 0.0);
-  const bool below = (double)f < s || ((double)f == s && e > 0.0);
-  if (dir < 0 && above) f = std::nextafter(f, -INFINITY);
-  if (dir > 0 && below) f = std::nextafter(f, INFINITY);
-  return f;
-}
-// float products are exact in double (24 + 24 significant bits)
-float mul_rd_f32(float a, float b) { return round_dir((double)a * (double)b, 0.0, -1); }
-// a + b in double with Knuth's TwoSum error term
-static float add_dir(float a, float b, int dir) {
-  const double x = a, y = b, s = x + y;
-  if (!std::isfinite(s)) return (float)s;
-  const double bb = s - x, e = (x - (s - bb)) + (y - bb);
-  return round_dir(s, e, dir);
-}
-float add_rd_f32(float a, float b) { return add_dir(a, b, -1); }
-float sub_rd_f32(float a, float b) { return add_dir(a, -b, -1); }
-float sub_ru_f32(float a, float b) { return add_dir(a, -b, +1); }
-// largest float f with f * d <= n (n >= 0, d > 0 finite): the quotient
-// rounded toward -inf; f * d is exact in double
-static float div_rd_f32(float n, float d) {
-  float f = (float)((double)n / (double)d);
-  while (f > 0.0f && (double)f * (double)d > (double)n) f = std::nextafter(f, -INFINITY);
-  for (int i = 0; i < 4; ++i) {
-    const float g = std::nextafter(f, INFINITY);
-    if (std::isfinite(g) && (double)g * (double)d <= (double)n) f = g;
-    else break;
-  }
-  return f;
-}
-
-// ---- world-grid codecs of the quantised own-box node (q16, eq10)
-// q16: coordinate = fma(code, step, wlo), the device arithmetic.
-float q16_decode(uint32_t q, float step, float wlo) { return std::fma((float)q, step, wlo); }
-// fma with directed rounding: code * bin is exact in double (10 + 24 bits),
-// the sum with TwoSum
-static float fma_dir(double p, float c, int dir) {
-  const double y = c, s = p + y;
-  if (!std::isfinite(s)) return (float)s;
-  const double bb = s - p, e = (p - (s - bb)) + (y - bb);
-  return round_dir(s, e, dir);
-}
-// eq10: lo = rd(code * bin + wlo), hi = ru(whi - code * bin), one rounding each.
-float eq10_decode_lo(uint32_t q, float bin, float wlo) { return fma_dir((double)q * (double)bin, wlo, -1); }
-float eq10_decode_hi(uint32_t q, float bin, float whi) { return fma_dir(-(double)q * (double)bin, whi, +1); }
-
-// q16 frame of one axis: the smallest step (from extent / 65535 up) whose
-// last code reaches whi.
-static float q16_step(float wlo, float whi) {
-  const double ext = (double)whi - (double)wlo;
-  if (!(ext > 0.0)) return 0.0f;
-  float step = round_up_f32(ext / (double)kQ16Max);
-  while (q16_decode(kQ16Max, step, wlo) < whi) step = std::nextafter(step, INFINITY);
-  return step;
-}
-// eq10 frame of one axis (App. D.1 construct_bins_inverse / construct_bins):
-// bins_inv = rd(1023 / ru(whi - wlo)) (1 for an empty extent), bin = rd(1 / bins_inv).
-static void eq10_bins(float wlo, float whi, float *bin, float *bins_inv) {
-  float L = sub_ru_f32(whi, wlo);
-  if (!(L > 0.0f)) L = 1.0f;
-  *bins_inv = div_rd_f32((float)kEq10Max, L);
-  *bin = *bins_inv > 0.0f ? div_rd_f32(1.0f, *bins_inv) : 0.0f;
-}
-static uint32_t clamp_code(double v, uint32_t qmax) {
-  if (!(v > 0.0)) return 0;
-  if (v >= (double)qmax) return qmax;
-  return (uint32_t)v;
-}
-// Codes of one axis of a box; the decoded interval always encloses [lo, hi]
-// (verify-and-bump against the exact device decode). Returns false if not.
-static bool q16_codes(float lo, float hi, float step, float wlo, uint32_t *qlo, uint32_t *qhi) {
-  uint32_t a = 0, b = 0;
-  if (step > 0.0f) {
-    a = clamp_code(std::floor(((double)lo - (double)wlo) / (double)step), kQ16Max);
-    b = clamp_code(std::ceil(((double)hi - (double)wlo) / (double)step), kQ16Max);
-  }
-  while (a > 0 && q16_decode(a, step, wlo) > lo) --a;
-  while (b < kQ16Max && q16_decode(b, step, wlo) < hi) ++b;
-  *qlo = a;
-  *qhi = b;
-  return q16_decode(a, step, wlo) <= lo && q16_decode(b, step, wlo) >= hi;
-}
-// eq10 codes: the App. D.1 quantize_lo / quantize_hi (floor of the directed
-// products), then verify-and-bump; hi codes count down from whi.
-static bool eq10_codes(float lo, float hi, float bin, float bins_inv, float wlo, float whi, uint32_t *qlo,
-                       uint32_t *qhi) {
-  uint32_t a = clamp_code(std::floor((double)mul_rd_f32(sub_rd_f32(lo, wlo), bins_inv)), kEq10Max);
-  uint32_t b = clamp_code(std::floor((double)mul_rd_f32(sub_rd_f32(whi, hi), bins_inv)), kEq10Max);
-  while (a > 0 && eq10_decode_lo(a, bin, wlo) > lo) --a;
-  while (b > 0 && eq10_decode_hi(b, bin, whi) < hi) --b;
-  *qlo = a;
-  *qhi = b;
-  return eq10_decode_lo(a, bin, wlo) <= lo && eq10_decode_hi(b, bin, whi) >= hi;
-}
-
 // ------------------------------------------------------------ descriptor
 scion_status normalize_desc(const scion_layout_desc &in, scion_layout_desc *out, bool *own_box) {
   scion_layout_desc d = in;
@@ -646,36 +495,6 @@ std::vector<uint32_t> order_nodes(const OrderTree &t, uint32_t order, bool group
 
 float area_of(const Box3 &b) { return (float)box_area(b); }
 
-// World-space pad: 2^-20 * (largest extent + largest |coordinate|), applied
-// outward before any encoding so that the traversal's float slab test (with
-// its relative margin) never culls a box whose triangle the intersector hits.
-Box3 padded(const Box3 &b) {
-  double ext = 0.0, mag = 0.0;
-  for (int a = 0; a < 3; ++a) {
-    ext = std::max(ext, (double)b.hi[a] - (double)b.lo[a]);
-    mag = std::max(mag, std::max(std::fabs((double)b.lo[a]), std::fabs((double)b.hi[a])));
-  }
-  const double pad = std::ldexp(ext + mag, -20);
-  Box3 o;
-  for (int a = 0; a < 3; ++a) {
-    o.lo[a] = round_down_f32((double)b.lo[a] - pad);
-    o.hi[a] = round_up_f32((double)b.hi[a] + pad);
-  }
-  return o;
-}
-
-inline void put_u32(uint8_t *p, uint32_t v) { std::memcpy(p, &v, 4); }
-inline void put_f32(uint8_t *p, float v) { std::memcpy(p, &v, 4); }
-inline void put_u16(uint8_t *p, uint16_t v) { std::memcpy(p, &v, 2); }
-inline uint32_t get_u32(const uint8_t *p) { uint32_t v; std::memcpy(&v, p, 4); return v; }
-inline float get_f32(const uint8_t *p) { float v; std::memcpy(&v, p, 4); return v; }
-inline uint16_t get_u16(const uint8_t *p) { uint16_t v; std::memcpy(&v, p, 2); return v; }
-
-// u8 frame decode: coordinate = fma(q, 2^e, origin), the device arithmetic.
-inline float u8_decode(uint32_t q, float scale, float origin) {
-  return std::fma((float)q, scale, origin);
-}
-
 // Leaf entries [at, at + count) of a logical leaf, in the leaf's order.
 void emit_prims(const BuildInput &in, const LogicalBVH &lb, const LNode &leaf, HostBVH *out, uint32_t at) {
   for (uint32_t k = 0; k < leaf.count; ++k) {
@@ -797,23 +616,11 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
     if (ref_bytes) out->nodes2.assign((size_t)nl * ref_bytes, 0);
     // world grid over the padded root box: q16 {wlo, step}, eq10 {wlo, whi, bin}
     float bins_inv[3] = {0.f, 0.f, 0.f};
-    if (quant) {
-      const Box3 root = padded(lb.nodes[0].box);
-      for (int a = 0; a < 3; ++a) {
-        out->frame[a] = root.lo[a];
-        if (prec == PREC_Q16) {
-          out->frame[3 + a] = q16_step(root.lo[a], root.hi[a]);
-        } else {
-          out->frame[3 + a] = root.hi[a];
-          eq10_bins(root.lo[a], root.hi[a], &out->frame[6 + a], &bins_inv[a]);
-        }
-      }
-    }
+    if (quant) world_frame(prec, padded(lb.nodes[0].box), out->frame, bins_inv);
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (long long pi = 0; pi < (long long)nl; ++pi) {
       const LNode &nd = lb.nodes[ord[pi]];
-      const Box3 b = padded(nd.box);
       uint32_t ref, meta;
       if (nd.count > 0) {
         ref = pbase[pi];
@@ -831,35 +638,14 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
         meta = bin_pack_meta(0, nd.axis);
       }
       uint8_t *p = out->nodes.data() + pi * out->node_stride;
+      bad |= encode_own_box(prec, nd.box, out->frame, bins_inv, p) ? 0 : 2;
       if (!quant) {
-        for (int a = 0; a < 3; ++a) {
-          put_f32(p + 4 * a, b.lo[a]);
-          put_f32(p + 12 + 4 * a, b.hi[a]);
-        }
         uint8_t *q = soa ? out->nodes2.data() + pi * kBinRefBytes : p + 24;
         put_u32(q, ref);
         put_u32(q + 4, meta);
-        continue;
-      }
-      const uint32_t word = nd.count > 0 ? qbin_leaf(ref, nd.count) : qbin_interior(ref, nd.axis);
-      uint32_t qlo[3], qhi[3];
-      for (int a = 0; a < 3; ++a) {
-        const bool ok = prec == PREC_Q16
-                            ? q16_codes(b.lo[a], b.hi[a], out->frame[3 + a], out->frame[a], &qlo[a], &qhi[a])
-                            : eq10_codes(b.lo[a], b.hi[a], out->frame[6 + a], bins_inv[a], out->frame[a],
-                                         out->frame[3 + a], &qlo[a], &qhi[a]);
-        bad |= ok ? 0 : 2;
-      }
-      if (prec == PREC_Q16) {
-        for (int a = 0; a < 3; ++a) {
-          put_u16(p + 2 * a, (uint16_t)qlo[a]);
-          put_u16(p + 6 + 2 * a, (uint16_t)qhi[a]);
-        }
-        put_u32(soa ? out->nodes2.data() + pi * 4 : p + 12, word);
       } else {
-        put_u32(p, eq10_pack(qlo[0], qlo[1], qlo[2]));
-        put_u32(p + 4, eq10_pack(qhi[0], qhi[1], qhi[2]));
-        put_u32(p + 8, word);
+        const uint32_t word = nd.count > 0 ? qbin_leaf(ref, nd.count) : qbin_interior(ref, nd.axis);
+        put_u32(prec == PREC_Q16 ? (soa ? out->nodes2.data() + pi * 4 : p + 12) : p + 8, word);
       }
     }
     if (bad & 1) {
@@ -968,7 +754,7 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
     const WNode &w = wn[ord[pi]];
     uint8_t *p = out->nodes.data() + (size_t)pi * stride;
     Box3 cb[8];
-    for (uint32_t k = 0; k < w.n; ++k) cb[k] = padded(lb.nodes[w.child[k]].box);
+    for (uint32_t k = 0; k < w.n; ++k) cb[k] = lb.nodes[w.child[k]].box;
     // references and leaf primitives (slot order)
     uint32_t first_interior = kEmptyRef, rank = 0, at = pbase[pi];
     for (uint32_t k = 0; k < W; ++k) {
@@ -997,80 +783,7 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
       put_u32(p + ref_off + 4, pbase[pi]);
     }
     // boxes
-    if (prec == PREC_F32) {
-      for (uint32_t k = 0; k < W; ++k)
-        for (uint32_t c = 0; c < 6; ++c) {
-          float v = k < w.n ? (c < 3 ? cb[k].lo[c] : cb[k].hi[c - 3]) : (c < 3 ? INFINITY : -INFINITY);
-          put_f32(p + wide_box_offset(W, prec, soa, k, c), v);
-        }
-    } else if (prec == PREC_F16) {
-      for (uint32_t k = 0; k < W; ++k)
-        for (uint32_t c = 0; c < 6; ++c) {
-          uint16_t h;
-          if (k < w.n) {
-            h = c < 3 ? f32_to_f16_down(cb[k].lo[c]) : f32_to_f16_up(cb[k].hi[c - 3]);
-            const float dec = f16_to_f32(h);
-            const bool ok = c < 3 ? dec <= cb[k].lo[c] : dec >= cb[k].hi[c - 3];
-            if (!ok) bad |= 2;
-          } else {
-            h = c < 3 ? 0x7C00 : 0xFC00;  // +inf / -inf: empty
-          }
-          put_u16(p + wide_box_offset(W, prec, soa, k, c), h);
-        }
-    } else {
-      // u8 relative to the merged child box (App. D.2), with a guard band of
-      // 2^-20 (|coordinate| + extent) beyond the padded boxes, power-of-two
-      // scale per axis, and verify-and-bump against the device decode.
-      double mlo[3], mhi[3];
-      for (int a = 0; a < 3; ++a) {
-        mlo[a] = INFINITY;
-        mhi[a] = -INFINITY;
-        for (uint32_t k = 0; k < w.n; ++k) {
-          mlo[a] = std::min(mlo[a], (double)cb[k].lo[a]);
-          mhi[a] = std::max(mhi[a], (double)cb[k].hi[a]);
-        }
-      }
-      double mag = 0.0, ext = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        mag = std::max(mag, std::max(std::fabs(mlo[a]), std::fabs(mhi[a])));
-        ext = std::max(ext, mhi[a] - mlo[a]);
-      }
-      const double g = std::ldexp(mag + ext, -20);
-      float origin[3], scale[3];
-      for (int a = 0; a < 3; ++a) {
-        origin[a] = round_down_f32(mlo[a] - g);
-        const double fhi = (double)round_up_f32(mhi[a] + g);
-        const double span = fhi - (double)origin[a];
-        int e = -126;
-        if (span > 0.0) {
-          int ex;
-          std::frexp(span / 255.0, &ex);  // span/255 < 2^ex
-          e = std::max(-126, ex - 2);
-        }
-        while (e < 127 && std::ldexp(255.0, e) < span) ++e;
-        scale[a] = (float)std::ldexp(1.0, e);
-        put_f32(p + 4 * a, origin[a]);
-        p[12 + a] = (uint8_t)(e + 127);
-      }
-      for (uint32_t k = 0; k < W; ++k)
-        for (int a = 0; a < 3; ++a) {
-          uint32_t qlo = 255, qhi = 0;
-          if (k < w.n) {
-            const double tlo = (double)cb[k].lo[a] - g, thi = (double)cb[k].hi[a] + g;
-            const double fl = std::floor((tlo - origin[a]) / scale[a]);
-            const double fh = std::ceil((thi - origin[a]) / scale[a]);
-            qlo = (uint32_t)std::min(255.0, std::max(0.0, fl));
-            qhi = (uint32_t)std::min(255.0, std::max(0.0, fh));
-            while (qlo > 0 && (double)u8_decode(qlo, scale[a], origin[a]) > tlo) --qlo;
-            while (qhi < 255 && (double)u8_decode(qhi, scale[a], origin[a]) < thi) ++qhi;
-            if ((double)u8_decode(qlo, scale[a], origin[a]) > tlo ||
-                (double)u8_decode(qhi, scale[a], origin[a]) < thi)
-              bad |= 4;
-          }
-          p[wide_box_offset(W, prec, soa, k, a)] = (uint8_t)qlo;
-          p[wide_box_offset(W, prec, soa, k, 3 + a)] = (uint8_t)qhi;
-        }
-    }
+    bad |= encode_wide_boxes(W, prec, soa, cb, w.n, p);
   }
   if (bad & 1) { *err = "siblings not contiguous"; return SCION_ERR_UNSUPPORTED_LAYOUT; }
   if (bad & 2) { *err = "f16 enclosure"; return SCION_ERR_BAD_INPUT; }

@@ -12,13 +12,10 @@
 #include <vector>
 
 #include "../../include/scion.h"
+#include "codec.h"
 #include "layout.h"
 
 namespace scion {
-
-struct Box3 {
-  float lo[3], hi[3];
-};
 
 // Logical BVH2 node (the paper's BVH ADT): leaf iff count > 0.
 struct LNode {
@@ -80,22 +77,6 @@ void build_logical(const BuildInput &in, uint32_t bins, uint32_t leaf_max, Logic
 // Pack a logical BVH into the physical layout of `desc` (already normalized).
 scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_layout_desc &desc,
                       bool own_box, HostBVH *out, std::string *err);
-
-// Outward rounding helpers (exposed for tests through the debug ABI).
-float round_down_f32(double x);
-float round_up_f32(double x);
-uint16_t f32_to_f16_down(float x);
-uint16_t f32_to_f16_up(float x);
-float f16_to_f32(uint16_t h);
-// Exact emulation of the device's directed-rounding float ops, and the
-// world-grid decodes of the quantised own-box node (same results as the GPU).
-float mul_rd_f32(float a, float b);
-float add_rd_f32(float a, float b);
-float sub_rd_f32(float a, float b);
-float sub_ru_f32(float a, float b);
-float q16_decode(uint32_t q, float step, float wlo);
-float eq10_decode_lo(uint32_t q, float bin, float wlo);
-float eq10_decode_hi(uint32_t q, float bin, float whi);
 
 // Decode one packed node back to its logical view (round-trip check).
 struct DecodedChild {

@@ -112,6 +112,7 @@ def lib():
         L.scion_build.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), P, ctypes.POINTER(P)]
         L.scion_build_gpu.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), P, ctypes.POINTER(P)]
         L.scion_bvh_build_times.argtypes = [P, P, P]
+        L.scion_refit.argtypes = [P, P, U64, P]
         L.scion_bvh_info.argtypes = [P, P, P, P, P]
         L.scion_build_many.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), U32, P, ctypes.POINTER(P)]
         L.scion_trace_closest.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
@@ -140,8 +141,8 @@ def lib():
         L.scion_debug_f16_round.restype = U32
         L.scion_debug_f16_decode.argtypes = [U32]
         L.scion_debug_f16_decode.restype = ctypes.c_float
-        for name in ("scion_build", "scion_build_gpu", "scion_bvh_build_times", "scion_build_many",
-                     "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
+        for name in ("scion_build", "scion_build_gpu", "scion_bvh_build_times", "scion_refit",
+                     "scion_build_many", "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
                      "scion_trace_stats", "scion_trace_backward", "scion_batch_create",
                      "scion_batch_launch", "scion_batch_info", "scion_trace_batched",
                      "scion_get_status", "scion_debug_build_host", "scion_debug_host_stats",
@@ -239,6 +240,16 @@ def scion_build_gpu(verts, desc: LayoutDesc, indices=None, stream=None) -> BVH:
                                  None if ix is None else ctypes.c_void_p(ix.data_ptr()), nt,
                                  ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(h)), "scion_build_gpu")
     return BVH(h, nt, nv, desc)
+
+
+def scion_refit(bvh: BVH, verts, stream=None) -> None:
+    """Refit `bvh` to new vertex positions (float32 [n_verts, 3], CUDA tensor
+    or numpy array copied to the device): same triangles, same tree."""
+    import torch
+    v = torch.as_tensor(verts, dtype=torch.float32).cuda().contiguous()
+    _check(lib().scion_refit(bvh.handle, ctypes.c_void_p(v.data_ptr()), v.shape[0], _stream_ptr(stream)),
+           "scion_refit")
+    bvh._refit_src = v  # keep the source alive until the enqueued copies ran
 
 
 def scion_bvh_build_times(bvh: BVH) -> dict:
