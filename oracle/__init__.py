@@ -61,6 +61,9 @@ def _bind(path):
     L.oracle_plane_tuv.argtypes = [P, P, P, P, P, P]
     L.oracle_plane_tuv.restype = I
     L.oracle_max_threads.restype = I
+    L.oracle_cpq_brute.argtypes = [P, U64, P, U64, P, I]
+    L.oracle_closest_point.argtypes = [P, P, P, P, P]
+    L.oracle_closest_point.restype = I
     return L
 
 
@@ -76,27 +79,7 @@ def use_library(path):
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(LIB_PATH)
-        P = ctypes.c_void_p
-        U64 = ctypes.c_uint64
-        I = ctypes.c_int
-        L.oracle_intersect.argtypes = [P, P, P, P, P]
-        L.oracle_intersect.restype = I
-        L.oracle_closest_brute.argtypes = [P, U64, P, U64, P, I]
-        L.oracle_any_brute.argtypes = [P, U64, P, U64, P, I]
-        L.oracle_bvh_build.argtypes = [P, U64, I, I]
-        L.oracle_bvh_build.restype = P
-        L.oracle_bvh_closest.argtypes = [P, P, U64, P, I]
-        L.oracle_bvh_any.argtypes = [P, P, U64, P, I]
-        L.oracle_bvh_stats.argtypes = [P, P, P, P]
-        L.oracle_bvh_free.argtypes = [P]
-        L.oracle_grad.argtypes = [P, P, U64, P, P, P, U64, P, P]
-        L.oracle_grad_fd.argtypes = [P, P, U64, P, P, P, U64, ctypes.c_double, P, P]
-        L.oracle_plane_tuv.argtypes = [P, P, P, P, P, P]
-        L.oracle_plane_tuv.restype = I
-        L.oracle_max_threads.restype = I
-        _lib = L
+        _lib = _bind(build())
     return _lib
 
 
@@ -202,3 +185,24 @@ def plane_tuv(o, d, p0, p1, p2):
     out = np.zeros(3, np.float64)
     ok = lib().oracle_plane_tuv(*[_ptr(x) for x in a], _ptr(out))
     return tuple(out) if ok else None
+
+
+def closest_point(pt, tri):
+    """One point (3 floats) against one triangle (9 floats): (d2, u, v), or
+    None for a non-finite triangle."""
+    p = _f32(pt).reshape(3)
+    t = _f32(tri).reshape(9)
+    out = np.zeros(3, np.float32)
+    o = [out[i:i + 1] for i in range(3)]
+    ok = lib().oracle_closest_point(_ptr(p), _ptr(t), _ptr(o[0]), _ptr(o[1]), _ptr(o[2]))
+    return (float(out[0]), float(out[1]), float(out[2])) if ok else None
+
+
+def cpq_brute(tris, points, threads: int = 0) -> np.ndarray:
+    """Closest point query by brute force. points: float [n][4] (x, y, z,
+    r2max). Returns records (t = d2, u, v, prim) in the hit dtype."""
+    tris = _f32(tris).reshape(-1, 9)
+    pts = _f32(points).reshape(-1, 4)
+    out = np.zeros(pts.shape[0], HIT_DTYPE)
+    lib().oracle_cpq_brute(_ptr(tris), tris.shape[0], _ptr(pts), pts.shape[0], _ptr(out), threads)
+    return out

@@ -639,3 +639,138 @@ void oracle_grad_fd(const float *tris, const uint32_t *tri_verts, uint64_t n_ver
     if (gr) for (int k = 0; k < 6; ++k) gr[k] = dx[k];
   }
 }
+
+/* ------------------------------------------------------------------ closest point query
+ * The paper's second traversal algorithm (App. G "Closest Point Query"): for a
+ * query point p, the closest point on the closest triangle. The oracle fixes:
+ *  - result = lexicographic minimum of (d2_i, i) over all triangles i with a
+ *    finite vertex set and d2_i <= r2max (closed), d2_i the pinned squared
+ *    distance below; a miss is d2 = +inf, u = v = 0, prim = 0xFFFFFFFF;
+ *  - the closest point on a triangle by the Voronoi-region method of
+ *    Ericson, Real-Time Collision Detection (2005), Section 5.1.5 (the
+ *    reference App. G cites), in float with every product, sum and division
+ *    rounded in the order written here:
+ *      dot(x, y) = (x0*y0 + x1*y1) + x2*y2
+ *      ab = b - a, ac = c - a, ap = p - a; d1 = dot(ab, ap), d2 = dot(ac, ap)
+ *      vertex a: d1 <= 0 && d2 <= 0                        (u, v) = (0, 0)
+ *      bp = p - b; d3 = dot(ab, bp), d4 = dot(ac, bp)
+ *      vertex b: d3 >= 0 && d4 <= d3                        (1, 0)
+ *      vc = d1*d4 - d3*d2
+ *      edge ab: vc <= 0 && d1 >= 0 && d3 <= 0               s = d1/(d1 - d3); (s, 0), q = a + s*ab
+ *      cp = p - c; d5 = dot(ab, cp), d6 = dot(ac, cp)
+ *      vertex c: d6 >= 0 && d5 <= d6                        (0, 1)
+ *      vb = d5*d2 - d1*d6
+ *      edge ac: vb <= 0 && d2 >= 0 && d6 <= 0               s = d2/(d2 - d6); (0, s), q = a + s*ac
+ *      va = d3*d6 - d5*d4
+ *      edge bc: va <= 0 && d4 - d3 >= 0 && d5 - d6 >= 0    s = (d4 - d3)/((d4 - d3) + (d5 - d6));
+ *                                                           (1 - s, s), q = b + s*(c - b)
+ *      face: r = 1/((va + vb) + vc), v = vb*r, w = vc*r; (v, w), q = (a + ab*v) + ac*w
+ *    (u, v) are the barycentric weights of p1 and p2 of the closest point.
+ *    In the face case, v and w are first clamped to >= 0 and, if v + w > 1,
+ *    both divided by (v + w): exact arithmetic never needs this, but with
+ *    rounding the region tests can disagree with each other and the clamp
+ *    keeps q inside the triangle;
+ *      d2 = dot(p - q, p - q).
+ * The paper's listing also lowers the bound with a "distmax" of each box;
+ * that is not an upper bound on the distance to the nearest triangle for
+ * boxes that are not tight, so neither side uses it. */
+static float dot3f(const float *x, const float *y) { return (x[0] * y[0] + x[1] * y[1]) + x[2] * y[2]; }
+
+static float closest_on_tri(const float *p, const float *tri, float *u_out, float *v_out) {
+  const float *a = tri, *b = tri + 3, *c = tri + 6;
+  float ab[3], ac[3], ap[3], bp[3], cp[3], q[3];
+  for (int k = 0; k < 3; ++k) {
+    ab[k] = b[k] - a[k];
+    ac[k] = c[k] - a[k];
+    ap[k] = p[k] - a[k];
+  }
+  float u, v;
+  const float d1 = dot3f(ab, ap), d2 = dot3f(ac, ap);
+  if (d1 <= 0.0f && d2 <= 0.0f) {
+    u = 0.0f; v = 0.0f;
+    for (int k = 0; k < 3; ++k) q[k] = a[k];
+    goto done;
+  }
+  for (int k = 0; k < 3; ++k) bp[k] = p[k] - b[k];
+  const float d3 = dot3f(ab, bp), d4 = dot3f(ac, bp);
+  if (d3 >= 0.0f && d4 <= d3) {
+    u = 1.0f; v = 0.0f;
+    for (int k = 0; k < 3; ++k) q[k] = b[k];
+    goto done;
+  }
+  const float vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) {
+    const float s = d1 / (d1 - d3);
+    u = s; v = 0.0f;
+    for (int k = 0; k < 3; ++k) q[k] = a[k] + s * ab[k];
+    goto done;
+  }
+  for (int k = 0; k < 3; ++k) cp[k] = p[k] - c[k];
+  const float d5 = dot3f(ab, cp), d6 = dot3f(ac, cp);
+  if (d6 >= 0.0f && d5 <= d6) {
+    u = 0.0f; v = 1.0f;
+    for (int k = 0; k < 3; ++k) q[k] = c[k];
+    goto done;
+  }
+  const float vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) {
+    const float s = d2 / (d2 - d6);
+    u = 0.0f; v = s;
+    for (int k = 0; k < 3; ++k) q[k] = a[k] + s * ac[k];
+    goto done;
+  }
+  const float va = d3 * d6 - d5 * d4;
+  const float e43 = d4 - d3, e56 = d5 - d6;
+  if (va <= 0.0f && e43 >= 0.0f && e56 >= 0.0f) {
+    const float s = e43 / (e43 + e56);
+    u = 1.0f - s; v = s;
+    for (int k = 0; k < 3; ++k) q[k] = b[k] + s * (c[k] - b[k]);
+    goto done;
+  }
+  {
+    const float r = 1.0f / ((va + vb) + vc);
+    float fv = vb * r, fw = vc * r;
+    if (!(fv >= 0.0f)) fv = 0.0f;
+    if (!(fw >= 0.0f)) fw = 0.0f;
+    const float sum = fv + fw;
+    if (sum > 1.0f) {
+      fv = fv / sum;
+      fw = fw / sum;
+    }
+    u = fv; v = fw;
+    for (int k = 0; k < 3; ++k) q[k] = (a[k] + ab[k] * fv) + ac[k] * fw;
+  }
+done:;
+  float x[3];
+  for (int k = 0; k < 3; ++k) x[k] = p[k] - q[k];
+  *u_out = u;
+  *v_out = v;
+  return dot3f(x, x);
+}
+
+int oracle_closest_point(const float *pt, const float *tri, float *d2, float *u, float *v) {
+  if (!tri_finite(tri)) return 0;
+  *d2 = closest_on_tri(pt, tri, u, v);
+  return 1;
+}
+
+void oracle_cpq_brute(const float *tris, uint64_t n_tris, const float *pts, uint64_t n,
+                      oracle_hit *out, int threads) {
+  long long nn = (long long)n;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(pick_threads(threads))
+  for (long long r = 0; r < nn; ++r) {
+    const float *p = pts + 4 * r;
+    oracle_hit best;
+    miss_hit(&best);
+    for (uint64_t i = 0; i < n_tris; ++i) {
+      const float *tri = tris + 9 * i;
+      if (!tri_finite(tri)) continue;
+      float u, v;
+      const float d2 = closest_on_tri(p, tri, &u, &v);
+      if (d2 <= p[3] && better(d2, (uint32_t)i, best.t, best.prim)) {
+        best.t = d2; best.u = u; best.v = v; best.prim = (uint32_t)i;
+      }
+    }
+    out[r] = best;
+  }
+}

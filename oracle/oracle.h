@@ -78,6 +78,16 @@ void oracle_grad_fd(const float *tris, const uint32_t *tri_verts, uint64_t n_ver
 int oracle_plane_tuv(const double *o, const double *d, const double *p0,
                      const double *p1, const double *p2, double *tuv);
 
+/* Closest point query (App. G): for each point (x, y, z, r2max) the
+ * lexicographic minimum of (d2, id) over triangles with d2 <= r2max, d2 the
+ * squared distance to the pinned closest point on the triangle (Ericson 2005,
+ * Section 5.1.5; see oracle.c). out[i] = {d2, u, v, prim}: (u, v) weights of
+ * p1 and p2 of the closest point; miss = {inf, 0, 0, 0xFFFFFFFF}. */
+void oracle_cpq_brute(const float *tris, uint64_t n_tris, const float *pts, uint64_t n,
+                      oracle_hit *out, int threads);
+/* One point (3 floats) against one triangle; 0 if the triangle is not finite. */
+int oracle_closest_point(const float *pt, const float *tri, float *d2, float *u, float *v);
+
 int oracle_max_threads(void);
 
 #ifdef __cplusplus

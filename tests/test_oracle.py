@@ -350,3 +350,111 @@ def test_gradient_invariances_and_fd_config1(oracle_mod):
     np.testing.assert_allclose(fr4[hit], gr[hit], rtol=0, atol=1e-4 * rscale)
     assert np.abs(fv4 - gv).max() < 0.05 * np.abs(fv - gv).max()
     assert np.all(gr[~hit] == 0)
+
+
+# ------------------------------------------------------------------ closest point query
+def _seg_point_f64(p, a, b):
+    ab = b - a
+    den = ab @ ab
+    s = 0.0 if den == 0.0 else min(1.0, max(0.0, ((p - a) @ ab) / den))
+    return a + s * ab
+
+
+def _dist_f64(p, tri):
+    """Distance from p to a triangle in float64 by another method than the
+    oracle's: the plane projection if it falls inside the triangle
+    (barycentrics from normal equations), else the nearest of the three
+    clamped edge projections."""
+    a, b, c = (np.asarray(tri[3 * k:3 * k + 3], np.float64) for k in range(3))
+    p = np.asarray(p, np.float64)
+    e1, e2 = b - a, c - a
+    G = np.array([[e1 @ e1, e1 @ e2], [e1 @ e2, e2 @ e2]])
+    cands = [_seg_point_f64(p, a, b), _seg_point_f64(p, a, c), _seg_point_f64(p, b, c)]
+    if abs(np.linalg.det(G)) > 1e-12 * (e1 @ e1) * (e2 @ e2) + 1e-300:
+        s, t = np.linalg.solve(G, np.array([(p - a) @ e1, (p - a) @ e2]))
+        if s >= 0 and t >= 0 and s + t <= 1:
+            cands.append(a + s * e1 + t * e2)
+    return min(np.linalg.norm(p - q) for q in cands)
+
+
+@pytest.mark.parametrize("pt,exp", [
+    ((0.25, 0.25, 2.0), (4.0, 0.25, 0.25)),     # face: straight above the interior
+    ((-1.0, -1.0, 0.0), (2.0, 0.0, 0.0)),       # vertex p0
+    ((2.0, -1.0, 0.0), (2.0, 1.0, 0.0)),        # vertex p1
+    ((-0.5, 3.0, 0.0), (4.25, 0.0, 1.0)),       # vertex p2
+    ((0.5, -1.0, 0.0), (1.0, 0.5, 0.0)),        # edge p0p1
+    ((-1.0, 0.5, 3.0), (10.0, 0.0, 0.5)),       # edge p0p2
+    ((1.0, 1.0, 0.0), (0.5, 0.5, 0.5)),         # edge p1p2
+    ((0.25, 0.5, 0.0), (0.0, 0.25, 0.5)),       # on the triangle
+])
+def test_closest_point_closed_forms(oracle_mod, pt, exp):
+    """Dyadic cases in every Voronoi region of (0,0,0), (1,0,0), (0,1,0):
+    exact squared distance and barycentric weights of p1, p2."""
+    tri = [0, 0, 0, 1, 0, 0, 0, 1, 0]
+    assert oracle_mod.closest_point(pt, tri) == exp
+
+
+def test_closest_point_against_independent_f64(oracle_mod):
+    """Random triangles (including slivers and near-degenerate ones) and points
+    at several distances: the f32 result is within f32 rounding of the
+    float64 distance computed by another method, the weights lie in the
+    triangle, and they rebuild a point at that distance."""
+    rng = np.random.default_rng(11)
+    n_bad = 0
+    for i in range(3000):
+        tri = rng.normal(size=9) * (10.0 ** rng.uniform(-3, 2))
+        if i % 10 == 0:
+            tri[6:9] = tri[0:3] + (tri[3:6] - tri[0:3]) * rng.uniform(0, 1) + rng.normal(size=3) * 1e-4
+        tri = tri.astype(np.float32)
+        p = (tri[:3] + rng.normal(size=3) * (10.0 ** rng.uniform(-4, 2))).astype(np.float32)
+        d2, u, v = oracle_mod.closest_point(p, tri)
+        ref = _dist_f64(p, tri.astype(np.float64))
+        scale = float(np.abs(np.concatenate([tri, p])).max())
+        assert abs(math.sqrt(d2) - ref) <= 1e-5 * (ref + scale), (i, d2, ref * ref)
+        assert u >= 0 and v >= 0 and u + v <= 1 + 1e-6
+        a, b, c = (tri[3 * k:3 * k + 3].astype(np.float64) for k in range(3))
+        q = (1 - u - v) * a + u * b + v * c
+        n_bad += abs(np.linalg.norm(p - q) - math.sqrt(d2)) > 1e-4 * (ref + scale)
+    assert n_bad == 0
+
+
+def test_closest_point_degenerate_and_nonfinite(oracle_mod):
+    # a triangle collapsed to a segment, and to a point
+    seg = [0, 0, 0, 2, 0, 0, 1, 0, 0]
+    assert oracle_mod.closest_point((1.0, 3.0, 0.0), seg)[0] == 9.0
+    assert oracle_mod.closest_point((-2.0, 0.0, 0.0), seg)[0] == 4.0
+    pt = [1, 1, 1] * 3
+    assert oracle_mod.closest_point((1.0, 1.0, 3.0), pt)[0] == 4.0
+    assert oracle_mod.closest_point((0.0, 0.0, 0.0), [0, 0, 0, 1, 0, 0, float("nan"), 1, 0]) is None
+
+
+def test_cpq_brute_ties_radius_and_miss(oracle_mod):
+    """Lowest id among equal distances; only triangles with d2 <= r2max
+    count (closed); a NaN point or an empty scene gives a miss."""
+    base = np.array([0, 0, 0, 1, 0, 0, 0, 1, 0], np.float32)
+    far = base + np.array([0, 0, 5] * 3, np.float32)
+    tris = np.stack([far, base, base, far])
+    pts = np.array([[0.25, 0.25, 1.0, np.inf],   # nearest: the two copies of base, d2 = 1
+                    [0.25, 0.25, 1.0, 1.0],       # radius exactly 1: still found
+                    [0.25, 0.25, 1.0, 0.99],      # radius below: miss
+                    [0.25, 0.25, 4.0, np.inf],    # nearer to the far copies: id 0
+                    [np.nan, 0.0, 0.0, np.inf]], np.float32)
+    out = oracle_mod.cpq_brute(tris, pts)
+    assert list(out["prim"]) == [1, 1, 0xFFFFFFFF, 0, 0xFFFFFFFF]
+    assert out["t"][0] == 1.0 and out["t"][3] == 1.0 and math.isinf(out["t"][2])
+    assert out["u"][0] == 0.25 and out["v"][0] == 0.25
+    empty = oracle_mod.cpq_brute(np.zeros((0, 9), np.float32), pts[:1])
+    assert empty["prim"][0] == 0xFFFFFFFF
+
+
+def test_cpq_brute_is_the_minimum_over_triangles(oracle_mod):
+    """On a soup, the brute force equals the minimum of the single-triangle
+    evaluations (lexicographic in (d2, id))."""
+    rng = np.random.default_rng(5)
+    tris = scenes.random_soup(rng, 300, mu=math.log(0.05)).reshape(-1, 9)
+    pts = np.concatenate([rng.uniform(-0.2, 1.2, (64, 3)), np.full((64, 1), np.inf)], 1).astype(np.float32)
+    out = oracle_mod.cpq_brute(tris, pts)
+    for j in range(64):
+        d = [oracle_mod.closest_point(pts[j, :3], t)[0] for t in tris]
+        k = min(range(len(d)), key=lambda i: (d[i], i))
+        assert out["prim"][j] == k and out["t"][j] == d[k]

@@ -25,6 +25,11 @@ MUTANTS = {
     "grad_ray_t_scale": ("gr[3 + k] = -t * lam[k];", "gr[3 + k] = -lam[k];"),
     "bvh_visits_right_only": ("  visit(q, nd->left);\n  if (q->any && q->found) return;\n",
                               "  if (q->any && q->found) return;\n"),
+    "cpq_edge_bc_weights_swapped": ("u = 1.0f - s; v = s;", "u = s; v = 1.0f - s;"),
+    "cpq_vertex_b_region": ("if (d3 >= 0.0f && d4 <= d3) {", "if (d3 >= 0.0f && d4 >= d3) {"),
+    "cpq_dot_drops_z": ("return (x[0] * y[0] + x[1] * y[1]) + x[2] * y[2];", "return x[0] * y[0] + x[1] * y[1];"),
+    "cpq_radius_open": ("if (d2 <= p[3] && better(", "if (d2 < p[3] && better("),
+    "cpq_face_weights_swapped": ("u = fv; v = fw;", "u = fw; v = fv;"),
 }
 
 PINS = ["tests/test_oracle.py"]
