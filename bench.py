@@ -434,6 +434,57 @@ def time_query(scion, torch, bvh, fn, rays, out, steps, warmup):
     return trimmed_mean(ts), mode
 
 
+# ------------------------------------------------------------------ closest point query
+def bench_cpq(scion, torch, steps, warmup, hbm_peak):
+    """Closest point query (App. G): 2^20 points uniform in the coherent
+    scene's box (the paper's query count), unbounded radius, on the swept
+    layouts with direct triangles; throughput, visits and the algorithmic
+    bytes fraction of the measured HBM bandwidth."""
+    from paper_2511_15028_gb300 import scenes
+    sc = scenes.config2_scene()
+    rng = np.random.default_rng(2005)
+    lo, hi = sc.verts.min(0) - 0.1, sc.verts.max(0) + 0.1
+    n = 1 << 20
+    pts = torch.from_numpy(np.concatenate([lo + (hi - lo) * rng.uniform(size=(n, 3)), np.full((n, 1), np.inf)],
+                                          1).astype(np.float32)).cuda()
+    out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    res = {}
+    for name, desc in scion.sweep_layouts(quantised_bvh2=True).items():
+        if name.endswith("indirect"):
+            continue
+        bvh = scion.scion_build(sc.verts, desc, sc.indices)
+        _, c = scion.scion_trace_stats(bvh, pts, 2)
+        c = c.cpu().numpy()
+        # an own-box visit reads its node and both children's nodes (the
+        # children's boxes are bounded at the parent); a wide visit one node
+        own = desc.width == 2 and desc.box_prec in (0, 3, 4)
+        alg = (int(c[3]) * 32 + int(c[0]) * node_load_bytes(desc) * (3 if own else 1)
+               + int(c[2]) * tri_load_bytes(desc, True))
+        best, best_ms = None, None
+        for mode, p in (("sorted", None), ("slot_order", {"ordered_children": 2})):
+            scion.scion_query_closest_point(bvh, pts, out, params=p)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(warmup + steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                scion.scion_query_closest_point(bvh, pts, out, params=p)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = trimmed_mean(ts[warmup:])
+            if best_ms is None or ms < best_ms:
+                best, best_ms = mode, ms
+        info = scion.scion_bvh_info(bvh)
+        res[name] = {"mpoints_s": n / (best_ms / 1e3) / 1e6, "ms": best_ms, "order": best,
+                     "bvh_mb": (info["node_bytes"] + info["prim_bytes"]) / 1e6,
+                     "nodes_per_point": float(c[0]) / n, "tris_per_point": float(c[2]) / n,
+                     "alg_frac_of_measured_hbm": alg / (best_ms / 1e3) / 1e9 / hbm_peak}
+        del bvh
+    return {"points": n, "layouts": res,
+            "pareto": pareto({k: (v["bvh_mb"], v["mpoints_s"]) for k, v in res.items()})}
+
+
 # ------------------------------------------------------------------ GPU construction
 def bench_build(scion, torch, steps, warmup):
     """Logical-BVH2 construction on the host (binned SAH, all host cores) and
@@ -633,7 +684,7 @@ def main():
     ap.add_argument("--layouts", default="all", help="all | comma-separated sweep names")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the incoherent, batched and backward measurements")
-    ap.add_argument("--section", default="all", choices=["all", "incoherent", "build"],
+    ap.add_argument("--section", default="all", choices=["all", "incoherent", "build", "cpq"],
                     help="incoherent: only the 2^23-triangle section (for profiling); "
                          "build: only the host/GPU construction section")
     args = ap.parse_args()
@@ -660,6 +711,14 @@ def main():
     from paper_2511_15028_gb300 import build as native_build
     native_build.build()
     from paper_2511_15028_gb300 import scion
+
+    if args.section == "cpq":
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peak = json.load(open(pk)).get("hbm_gbs", 6800.0) if os.path.exists(pk) else 6800.0
+        res = bench_cpq(scion, torch, args.steps, args.warmup, peak)
+        if rank == 0:
+            print(json.dumps({"section": "cpq", "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
+        return
 
     if args.section == "build":
         res = bench_build(scion, torch, args.steps, args.warmup)
@@ -775,6 +834,7 @@ def main():
         extra["batched"] = bench_batched(scion, torch, args.steps, args.warmup, flush_buf)
         extra["backward"] = bench_backward(scion, torch, args.steps, args.warmup)
         extra["build"] = bench_build(scion, torch, args.steps, args.warmup)
+        extra["closest_point"] = bench_cpq(scion, torch, args.steps, args.warmup, hbm_peak)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

@@ -140,6 +140,22 @@ typedef struct {
       rays_per_fetch, max_steps, reserved;
 } scion_trace_params;
 
+/* A closest point query (App. G "Closest Point Query"): a point and a squared
+ * search radius; only triangles with d2 <= r2max count (+inf: unbounded).
+ * 16 bytes, 16-byte aligned arrays. */
+typedef struct {
+  float x, y, z, r2max;
+} scion_point;
+
+/* A closest point: squared distance d2 to the closest point on triangle
+ * `prim`, whose barycentric weights of p1 and p2 are u and v. A miss (no
+ * triangle within the radius, or a point that is not finite) is d2 = +inf,
+ * u = v = 0, prim = SCION_PRIM_MISS. 16 bytes. */
+typedef struct {
+  float d2, u, v;
+  uint32_t prim;
+} scion_closest_point;
+
 typedef struct scion_bvh_s *scion_bvh;
 
 /* Build a BVH (Section 5.1 two-phase construction: binned-SAH logical BVH2,
@@ -249,11 +265,31 @@ scion_status scion_trace_backward(scion_bvh bvh, const scion_ray *d_rays, const 
                                   const float *d_grad_tuv, uint64_t n, float *d_grad_verts,
                                   scion_ray *d_grad_rays, scion_stream stream);
 
-/* Counting variant of the two traces, for measurement: the same results
+/* Closest point on the scene for each query point (App. G "Closest Point
+ * Query", on any layout of the BVH): the lexicographic minimum of (d2, id)
+ * over the triangles with d2 <= r2max, d2 the squared distance to the closest
+ * point on the triangle by the Voronoi-region method (Ericson 2005, Section
+ * 5.1.5) in float with a fixed rounding order (results are identical on
+ * every layout). Node boxes are bounded from below with outward rounding, so
+ * no box that could hold the winner is skipped; the paper's "distmax" bound
+ * update is not used.
+ *  d_points : device scion_point[n] (16-byte aligned).
+ *  d_out    : device scion_closest_point[n] (16-byte aligned).
+ *  params   : as scion_trace_closest (ordered_children: 0/1 children sorted
+ *             by box distance, 2 slot order, 3 nearest first); rays_per_fetch
+ *             must be 0 or 32.
+ * Asynchronous on `stream`; errors and device status as scion_trace_closest. */
+scion_status scion_query_closest_point(scion_bvh bvh, const scion_point *d_points, uint64_t n,
+                                      scion_closest_point *d_out, const scion_trace_params *params,
+                                      scion_stream stream);
+
+/* Counting variant of the traces, for measurement: the same results
  * (query 0: closest hits into scion_hit[n]; query 1: any-hit flags into
- * uint32[n]) plus visit counters added into d_counters (device uint64[4]):
- * [0] interior nodes fetched, [1] leaves visited, [2] triangles tested,
- * [3] rays traced. Slower than the plain calls; not for production use. */
+ * uint32[n]; query 2: closest points, d_rays then holding scion_point[n] and
+ * d_out scion_closest_point[n]) plus visit counters added into d_counters
+ * (device uint64[4]): [0] interior nodes fetched, [1] leaves visited,
+ * [2] triangles tested, [3] rays (points) traced. Slower than the plain
+ * calls; not for production use. */
 scion_status scion_trace_stats(scion_bvh bvh, const scion_ray *d_rays, uint64_t n, uint32_t query,
                                void *d_out, const scion_trace_params *params, scion_stream stream,
                                uint64_t *d_counters);

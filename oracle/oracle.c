@@ -645,7 +645,8 @@ void oracle_grad_fd(const float *tris, const uint32_t *tri_verts, uint64_t n_ver
  * query point p, the closest point on the closest triangle. The oracle fixes:
  *  - result = lexicographic minimum of (d2_i, i) over all triangles i with a
  *    finite vertex set and d2_i <= r2max (closed), d2_i the pinned squared
- *    distance below; a miss is d2 = +inf, u = v = 0, prim = 0xFFFFFFFF;
+ *    distance below; a miss is d2 = +inf, u = v = 0, prim = 0xFFFFFFFF; a
+ *    query point with a non-finite coordinate has no closest point (miss);
  *  - the closest point on a triangle by the Voronoi-region method of
  *    Ericson, Real-Time Collision Detection (2005), Section 5.1.5 (the
  *    reference App. G cites), in float with every product, sum and division
@@ -762,7 +763,9 @@ void oracle_cpq_brute(const float *tris, uint64_t n_tris, const float *pts, uint
     const float *p = pts + 4 * r;
     oracle_hit best;
     miss_hit(&best);
-    for (uint64_t i = 0; i < n_tris; ++i) {
+    /* a point that is not finite has no closest point */
+    const int live = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]);
+    for (uint64_t i = 0; live && i < n_tris; ++i) {
       const float *tri = tris + 9 * i;
       if (!tri_finite(tri)) continue;
       float u, v;

@@ -129,9 +129,39 @@ void bvh_args(const scion_bvh b, TraceArgs &a) {
   for (int k = 0; k < 9; ++k) a.frame[k] = b->frame[k];
 }
 
-TraceKernel pick_kernel(const scion_bvh b, int any, int stats) {
+// Query kinds of launch_trace.
+constexpr int kQueryClosest = 0, kQueryAny = 1, kQueryPoint = 2;
+
+TraceKernel pick_cpq_kernel(const scion_bvh b, int stats) {
   const scion_layout_desc &d = b->desc;
   const int soa = (int)d.box_layout, cref = (int)d.child_ref;
+  if (b->own_box) {
+    switch (d.box_prec) {
+      case PREC_F32: return cpq_kernels_own_p0(soa, cref, stats);
+      case PREC_Q16: return cpq_kernels_own_p3(soa, cref, stats);
+      case PREC_EQ10: return cpq_kernels_own_p4(soa, cref, stats);
+    }
+    return nullptr;
+  }
+  switch (d.width * 10 + d.box_prec) {
+    case 20: return cpq_kernels_w2_p0(soa, cref, stats);
+    case 21: return cpq_kernels_w2_p1(soa, cref, stats);
+    case 22: return cpq_kernels_w2_p2(soa, cref, stats);
+    case 40: return cpq_kernels_w4_p0(soa, cref, stats);
+    case 41: return cpq_kernels_w4_p1(soa, cref, stats);
+    case 42: return cpq_kernels_w4_p2(soa, cref, stats);
+    case 80: return cpq_kernels_w8_p0(soa, cref, stats);
+    case 81: return cpq_kernels_w8_p1(soa, cref, stats);
+    case 82: return cpq_kernels_w8_p2(soa, cref, stats);
+  }
+  return nullptr;
+}
+
+TraceKernel pick_kernel(const scion_bvh b, int query, int stats) {
+  const scion_layout_desc &d = b->desc;
+  const int soa = (int)d.box_layout, cref = (int)d.child_ref;
+  if (query == kQueryPoint) return pick_cpq_kernel(b, stats);
+  const int any = query == kQueryAny ? 1 : 0;
   if (b->own_box) {
     switch (d.box_prec) {
       case PREC_F32: return kernels_own_p0(soa, cref, any, stats);
@@ -259,24 +289,29 @@ int device_sms(int dev) {
 }
 
 scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *out,
-                          const scion_trace_params *params, cudaStream_t stream, int any,
+                          const scion_trace_params *params, cudaStream_t stream, int query,
                           unsigned long long *stats = nullptr) {
   if (!b || (n > 0 && (!rays || !out))) return SCION_ERR_INVALID_ARG;
   if (n == 0) return SCION_OK;
-  if ((reinterpret_cast<uintptr_t>(rays) & 15u) || (!any && (reinterpret_cast<uintptr_t>(out) & 15u)) ||
-      (any && (reinterpret_cast<uintptr_t>(out) & 3u)))
+  const bool out16 = query != kQueryAny;  // scion_hit / scion_closest_point records
+  if ((reinterpret_cast<uintptr_t>(rays) & 15u) || (out16 && (reinterpret_cast<uintptr_t>(out) & 15u)) ||
+      (!out16 && (reinterpret_cast<uintptr_t>(out) & 3u)))
     return SCION_ERR_INVALID_ARG;
   scion_trace_params p{};
   if (params) p = *params;
   if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch > 32)
     return SCION_ERR_INVALID_ARG;
+  if (query == kQueryPoint && p.rays_per_fetch != 0 && p.rays_per_fetch != 32) {
+    g_last_error = "closest point queries take 32-point warp batches only (rays_per_fetch 0 or 32)";
+    return SCION_ERR_INVALID_ARG;
+  }
   uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
   uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
   if (smem_entries > 64) return SCION_ERR_INVALID_ARG;
   if (p.ordered_children > 3) return SCION_ERR_INVALID_ARG;
   const uint32_t ordered = order_mode(p.ordered_children);
-  TraceKernel k = pick_kernel(b, any, stats ? 1 : 0);
+  TraceKernel k = pick_kernel(b, query, stats ? 1 : 0);
   if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
   const size_t smem = (size_t)tpb * smem_entries * sizeof(uint2);
   int dev = 0;
@@ -576,18 +611,25 @@ scion_status scion_bvh_info(scion_bvh b, uint64_t *node_bytes, uint64_t *prim_by
 
 scion_status scion_trace_closest(scion_bvh b, const scion_ray *d_rays, uint64_t n, scion_hit *d_hits,
                                  const scion_trace_params *params, scion_stream stream) {
-  return launch_trace(b, d_rays, n, d_hits, params, reinterpret_cast<cudaStream_t>(stream), 0);
+  return launch_trace(b, d_rays, n, d_hits, params, reinterpret_cast<cudaStream_t>(stream), kQueryClosest);
 }
 
 scion_status scion_trace_any(scion_bvh b, const scion_ray *d_rays, uint64_t n, uint32_t *d_occluded,
                              const scion_trace_params *params, scion_stream stream) {
-  return launch_trace(b, d_rays, n, d_occluded, params, reinterpret_cast<cudaStream_t>(stream), 1);
+  return launch_trace(b, d_rays, n, d_occluded, params, reinterpret_cast<cudaStream_t>(stream), kQueryAny);
+}
+
+scion_status scion_query_closest_point(scion_bvh b, const scion_point *d_points, uint64_t n,
+                                      scion_closest_point *d_out, const scion_trace_params *params,
+                                      scion_stream stream) {
+  return launch_trace(b, reinterpret_cast<const scion_ray *>(d_points), n, d_out, params,
+                      reinterpret_cast<cudaStream_t>(stream), kQueryPoint);
 }
 
 scion_status scion_trace_stats(scion_bvh b, const scion_ray *d_rays, uint64_t n, uint32_t query,
                               void *d_out, const scion_trace_params *params, scion_stream stream,
                               uint64_t *d_counters) {
-  if (!d_counters || query > 1 || (reinterpret_cast<uintptr_t>(d_counters) & 7u)) return SCION_ERR_INVALID_ARG;
+  if (!d_counters || query > 2 || (reinterpret_cast<uintptr_t>(d_counters) & 7u)) return SCION_ERR_INVALID_ARG;
   return launch_trace(b, d_rays, n, d_out, params, reinterpret_cast<cudaStream_t>(stream), (int)query,
                       reinterpret_cast<unsigned long long *>(d_counters));
 }
@@ -725,7 +767,7 @@ scion_status scion_batch_launch(scion_batch bt, scion_stream stream) {
                               bt->smem_stack, bt->threads, bt->grid, s));
   for (size_t i = 0; i < bt->rest_bvh.size(); ++i) {
     scion_status st = launch_trace(bt->rest_bvh[i], bt->rest_rays[i], bt->rest_n[i], bt->rest_hits[i],
-                                   &bt->rest_params[i], s, 0);
+                                   &bt->rest_params[i], s, kQueryClosest);
     if (st != SCION_OK) return st;
   }
   return SCION_OK;
@@ -928,7 +970,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
   const uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
   if (smem_entries > 64) return SCION_ERR_INVALID_ARG;
-  TraceKernel k = pick_kernel(b, 0, 0);
+  TraceKernel k = pick_kernel(b, kQueryClosest, 0);
   if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
   void *scratch = nullptr;
   scion_status st = static_scratch(&scratch);

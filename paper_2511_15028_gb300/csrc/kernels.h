@@ -24,6 +24,19 @@ TraceKernel kernels_w4_p2(int soa, int cref, int any, int stats);
 TraceKernel kernels_w8_p0(int soa, int cref, int any, int stats);
 TraceKernel kernels_w8_p1(int soa, int cref, int any, int stats);
 TraceKernel kernels_w8_p2(int soa, int cref, int any, int stats);
+// closest point query kernels of the same families
+TraceKernel cpq_kernels_own_p0(int soa, int cref, int stats);
+TraceKernel cpq_kernels_own_p3(int soa, int cref, int stats);
+TraceKernel cpq_kernels_own_p4(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w2_p0(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w2_p1(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w2_p2(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w4_p0(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w4_p1(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w4_p2(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w8_p0(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w8_p1(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w8_p2(int soa, int cref, int stats);
 
 constexpr int kMaxThreadsPerBlock = 256;
 // Four 256-thread CTAs per SM: caps a traversal kernel at 64 registers so 32

@@ -2,6 +2,7 @@
 // times with -DSCION_OWN=1 -DSCION_PREC=<0|3|4> (own-box node with f32, q16
 // or eq10 boxes), or -DSCION_W=<2|4|8> -DSCION_PREC=<0|1|2>, so the families
 // build in parallel.
+#include "cpq.cuh"
 #include "kernels.h"
 
 #define SCION_CAT_(a, b) a##b
@@ -13,9 +14,11 @@ namespace scion {
 #define SCION_FAMILY_OWN true
 #define SCION_W 2
 #define SCION_GETTER SCION_CAT(kernels_own_p, SCION_PREC)
+#define SCION_CPQ_GETTER SCION_CAT(cpq_kernels_own_p, SCION_PREC)
 #else
 #define SCION_FAMILY_OWN false
 #define SCION_GETTER SCION_CAT(SCION_CAT(SCION_CAT(kernels_w, SCION_W), _p), SCION_PREC)
+#define SCION_CPQ_GETTER SCION_CAT(SCION_CAT(SCION_CAT(cpq_kernels_w, SCION_W), _p), SCION_PREC)
 #endif
 
 template <int SOA, int CREF, bool ANY, bool STATS>
@@ -34,6 +37,18 @@ TraceKernel SCION_GETTER(int soa, int cref, int any, int stats) {
        {{trace_kernel<1, 1, false, false>, trace_kernel<1, 1, false, true>},
         {trace_kernel<1, 1, true, false>, trace_kernel<1, 1, true, true>}}}};
   return table[soa & 1][cref & 1][any & 1][stats & 1];
+}
+
+template <int SOA, int CREF, bool STATS>
+__global__ void __launch_bounds__(kMaxThreadsPerBlock, kMinBlocksPerSm) cpq_kernel(TraceArgs a) {
+  cpq_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, STATS>(a);
+}
+
+TraceKernel SCION_CPQ_GETTER(int soa, int cref, int stats) {
+  static const TraceKernel table[2][2][2] = {
+      {{cpq_kernel<0, 0, false>, cpq_kernel<0, 0, true>}, {cpq_kernel<0, 1, false>, cpq_kernel<0, 1, true>}},
+      {{cpq_kernel<1, 0, false>, cpq_kernel<1, 0, true>}, {cpq_kernel<1, 1, false>, cpq_kernel<1, 1, true>}}};
+  return table[soa & 1][cref & 1][stats & 1];
 }
 
 }  // namespace scion

@@ -113,6 +113,7 @@ def lib():
         L.scion_build_gpu.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), P, ctypes.POINTER(P)]
         L.scion_bvh_build_times.argtypes = [P, P, P]
         L.scion_refit.argtypes = [P, P, U64, P]
+        L.scion_query_closest_point.argtypes = [P, P, U64, P, P, P]
         L.scion_bvh_info.argtypes = [P, P, P, P, P]
         L.scion_build_many.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), U32, P, ctypes.POINTER(P)]
         L.scion_trace_closest.argtypes = [P, P, U64, P, ctypes.POINTER(TraceParams), P]
@@ -142,6 +143,7 @@ def lib():
         L.scion_debug_f16_decode.argtypes = [U32]
         L.scion_debug_f16_decode.restype = ctypes.c_float
         for name in ("scion_build", "scion_build_gpu", "scion_bvh_build_times", "scion_refit",
+                     "scion_query_closest_point",
                      "scion_build_many", "scion_bvh_info", "scion_trace_closest", "scion_trace_any",
                      "scion_trace_stats", "scion_trace_backward", "scion_batch_create",
                      "scion_batch_launch", "scion_batch_info", "scion_trace_batched",
@@ -329,14 +331,29 @@ def scion_trace_any(bvh: BVH, rays, occluded=None, params=None, stream=None):
     return occluded
 
 
+def scion_query_closest_point(bvh: BVH, points, out=None, params=None, stream=None):
+    """Closest points of device query points (float32 [n, 4]: x, y, z,
+    r2max); returns int32 [n, 4] holding (d2, u, v) as float bits and prim as
+    uint32 bits."""
+    import torch
+    assert points.is_cuda and points.dtype == torch.float32 and points.is_contiguous()
+    n = points.shape[0]
+    if out is None:
+        out = torch.empty((n, 4), dtype=torch.int32, device=points.device)
+    _check(lib().scion_query_closest_point(bvh.handle, ctypes.c_void_p(points.data_ptr()), n,
+                                           ctypes.c_void_p(out.data_ptr()), _params(params),
+                                           _stream_ptr(stream)), "scion_query_closest_point")
+    return out
+
+
 def scion_trace_stats(bvh: BVH, rays, query: int = 0, params=None, stream=None):
     """Counting trace: (results, counters) with counters = int64 tensor
     [nodes fetched, leaves visited, triangles tested, rays]."""
     import torch
     assert rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous()
     n = rays.shape[0]
-    out = (torch.empty((n, 4), dtype=torch.int32, device=rays.device) if query == 0
-           else torch.empty((n,), dtype=torch.int32, device=rays.device))
+    out = (torch.empty((n,), dtype=torch.int32, device=rays.device) if query == 1
+           else torch.empty((n, 4), dtype=torch.int32, device=rays.device))
     cnt = torch.zeros(4, dtype=torch.int64, device=rays.device)
     _check(lib().scion_trace_stats(bvh.handle, ctypes.c_void_p(rays.data_ptr()), n, query,
                                    ctypes.c_void_p(out.data_ptr()), _params(params), _stream_ptr(stream),

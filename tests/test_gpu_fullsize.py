@@ -101,3 +101,25 @@ def test_config3_full_size_gpu_built(sc_mod, oracle_mod):
         assert np.array_equal(occ, eocc)
         assert scion.scion_get_status(bvh) == 0
         del bvh
+
+
+def test_config2_full_size_closest_point(sc_mod, oracle_mod):
+    """2^20 query points in the coherent scene's box (the paper's CPQ point
+    count) on the swept layouts; 256 sampled points against brute force over
+    all 1,373,138 triangles."""
+    scion = sc_mod
+    sc = scenes.config2_scene()
+    rng = np.random.default_rng(2005)
+    lo, hi = sc.verts.min(0) - 0.1, sc.verts.max(0) + 0.1
+    pts = np.concatenate([lo + (hi - lo) * rng.uniform(size=(1 << 20, 3)), np.full((1 << 20, 1), np.inf)],
+                         1).astype(np.float32)
+    pick = np.sort(rng.choice(pts.shape[0], 256, replace=False))
+    exp = oracle_mod.cpq_brute(sc.triangles(), pts[pick])
+    d = torch.from_numpy(pts).cuda()
+    for name, desc in scion.sweep_layouts(quantised_bvh2=True).items():
+        if name.endswith("indirect"):
+            continue
+        bvh = scion.scion_build(sc.verts, desc, sc.indices)
+        got = scion.scion_query_closest_point(bvh, d)[torch.from_numpy(pick).cuda()]
+        _cmp(scion, got, exp, name + " closest point")
+        assert scion.scion_get_status(bvh) == 0

@@ -430,7 +430,8 @@ def test_closest_point_degenerate_and_nonfinite(oracle_mod):
 
 def test_cpq_brute_ties_radius_and_miss(oracle_mod):
     """Lowest id among equal distances; only triangles with d2 <= r2max
-    count (closed); a NaN point or an empty scene gives a miss."""
+    count (closed); a point with a non-finite coordinate or an empty scene
+    gives a miss."""
     base = np.array([0, 0, 0, 1, 0, 0, 0, 1, 0], np.float32)
     far = base + np.array([0, 0, 5] * 3, np.float32)
     tris = np.stack([far, base, base, far])
@@ -438,9 +439,10 @@ def test_cpq_brute_ties_radius_and_miss(oracle_mod):
                     [0.25, 0.25, 1.0, 1.0],       # radius exactly 1: still found
                     [0.25, 0.25, 1.0, 0.99],      # radius below: miss
                     [0.25, 0.25, 4.0, np.inf],    # nearer to the far copies: id 0
-                    [np.nan, 0.0, 0.0, np.inf]], np.float32)
+                    [np.nan, 0.0, 0.0, np.inf],   # a point that is not finite: miss
+                    [np.inf, 0.0, 0.0, np.inf]], np.float32)
     out = oracle_mod.cpq_brute(tris, pts)
-    assert list(out["prim"]) == [1, 1, 0xFFFFFFFF, 0, 0xFFFFFFFF]
+    assert list(out["prim"]) == [1, 1, 0xFFFFFFFF, 0, 0xFFFFFFFF, 0xFFFFFFFF]
     assert out["t"][0] == 1.0 and out["t"][3] == 1.0 and math.isinf(out["t"][2])
     assert out["u"][0] == 0.25 and out["v"][0] == 0.25
     empty = oracle_mod.cpq_brute(np.zeros((0, 9), np.float32), pts[:1])
