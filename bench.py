@@ -55,8 +55,8 @@ def node_load_bytes(desc) -> int:
         return 16
     if prec == 4:  # eq10 own-box node: 12 B (16 B aligned)
         return 16 if desc.align == 16 else 12
-    elem = {0: 4, 1: 2, 2: 1}[prec]
-    used = (16 if prec == 2 else 0) + w * 6 * elem + (4 * w if cref == 0 else 8 + w)
+    elem = {0: 4, 1: 2, 2: 1, 5: 2}[prec]
+    used = (16 if prec in (2, 5) else 0) + w * 6 * elem + (4 * w if cref == 0 else 8 + w)
     return (used + 15) // 16 * 16
 
 
@@ -365,7 +365,7 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
     short = rays.clone()
     short[:, 7] = 0.05
     gen_s = time.time() - t0
-    lays = scion.sweep_layouts(quantised_bvh2=True)
+    lays = scion.sweep_layouts(extended=True)
     if only:
         lays = {k: v for k, v in lays.items() if k in only}
     t0 = time.time()
@@ -449,7 +449,7 @@ def bench_cpq(scion, torch, steps, warmup, hbm_peak):
                                           1).astype(np.float32)).cuda()
     out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
     res = {}
-    for name, desc in scion.sweep_layouts(quantised_bvh2=True).items():
+    for name, desc in scion.sweep_layouts(extended=True).items():
         if name.endswith("indirect"):
             continue
         bvh = scion.scion_build(sc.verts, desc, sc.indices)
@@ -735,7 +735,7 @@ def main():
             print(json.dumps({"section": "incoherent", "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
         return
 
-    layouts = scion.sweep_layouts(quantised_bvh2=True)
+    layouts = scion.sweep_layouts(extended=True)
     if args.layouts != "all":
         keep = args.layouts.split(",")
         layouts = {k: v for k, v in layouts.items() if k in keep}

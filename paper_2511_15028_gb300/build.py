@@ -27,7 +27,7 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-fn
              "-Wall", "-I", INCLUDE]
 
 FAMILIES = [(f"own_p{p}", ["-DSCION_OWN=1", f"-DSCION_PREC={p}"]) for p in (0, 3, 4)] + [
-    (f"w{w}_p{p}", [f"-DSCION_W={w}", f"-DSCION_PREC={p}"]) for w in (2, 4, 8) for p in (0, 1, 2)]
+    (f"w{w}_p{p}", [f"-DSCION_W={w}", f"-DSCION_PREC={p}"]) for w in (2, 4, 8) for p in (0, 1, 2, 5)]
 
 
 def _sources():

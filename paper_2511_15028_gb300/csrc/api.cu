@@ -153,6 +153,9 @@ TraceKernel pick_cpq_kernel(const scion_bvh b, int stats) {
     case 80: return cpq_kernels_w8_p0(soa, cref, stats);
     case 81: return cpq_kernels_w8_p1(soa, cref, stats);
     case 82: return cpq_kernels_w8_p2(soa, cref, stats);
+    case 25: return cpq_kernels_w2_p5(soa, cref, stats);
+    case 45: return cpq_kernels_w4_p5(soa, cref, stats);
+    case 85: return cpq_kernels_w8_p5(soa, cref, stats);
   }
   return nullptr;
 }
@@ -180,6 +183,9 @@ TraceKernel pick_kernel(const scion_bvh b, int query, int stats) {
     case 80: return kernels_w8_p0(soa, cref, any, stats);
     case 81: return kernels_w8_p1(soa, cref, any, stats);
     case 82: return kernels_w8_p2(soa, cref, any, stats);
+    case 25: return kernels_w2_p5(soa, cref, any, stats);
+    case 45: return kernels_w4_p5(soa, cref, any, stats);
+    case 85: return kernels_w8_p5(soa, cref, any, stats);
   }
   return nullptr;
 }

@@ -20,7 +20,7 @@ scion_status normalize_desc(const scion_layout_desc &in, scion_layout_desc *out,
   scion_layout_desc d = in;
   if (d.align != 0 && d.align != 16) return SCION_ERR_INVALID_ARG;
   if (d.width != 2 && d.width != 4 && d.width != 8) return SCION_ERR_UNSUPPORTED_LAYOUT;
-  if (d.box_layout > 1 || d.box_prec > PREC_EQ10 || d.child_ref > 1 || d.prim_ref > 1 || d.order > 2)
+  if (d.box_layout > 1 || d.box_prec > PREC_U16 || d.child_ref > 1 || d.prim_ref > 1 || d.order > 2)
     return SCION_ERR_UNSUPPORTED_LAYOUT;
   if (d.leaf_max == 0) d.leaf_max = 4;
   if (d.leaf_max > kMaxLeaf) return SCION_ERR_UNSUPPORTED_LAYOUT;
@@ -787,7 +787,7 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
   }
   if (bad & 1) { *err = "siblings not contiguous"; return SCION_ERR_UNSUPPORTED_LAYOUT; }
   if (bad & 2) { *err = "f16 enclosure"; return SCION_ERR_BAD_INPUT; }
-  if (bad & 4) { *err = "u8 enclosure"; return SCION_ERR_BAD_INPUT; }
+  if (bad & 4) { *err = "u8/u16 enclosure"; return SCION_ERR_BAD_INPUT; }
   out->root_ref = ref_interior(0);
   out->depth = tree_depth(t, ord);
   out->stack_need = (W - 1) * out->depth + 1;
@@ -873,8 +873,10 @@ int decode_node(const HostBVH &b, uint32_t node, DecodedChild *ch, Box3 *own) {
         uint32_t bits = (uint32_t)p[12 + a] << 23;
         float scale;
         std::memcpy(&scale, &bits, 4);
-        c.box.lo[a] = u8_decode(p[olo], scale, origin);
-        c.box.hi[a] = u8_decode(p[ohi], scale, origin);
+        const uint32_t ql = prec == PREC_U8 ? p[olo] : get_u16(p + olo);
+        const uint32_t qh = prec == PREC_U8 ? p[ohi] : get_u16(p + ohi);
+        c.box.lo[a] = u8_decode(ql, scale, origin);
+        c.box.hi[a] = u8_decode(qh, scale, origin);
       }
     }
   }

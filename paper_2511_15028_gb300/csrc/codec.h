@@ -251,12 +251,12 @@ SCION_HD bool encode_own_box(uint32_t prec, const Box3 &exact, const float *fram
 }
 
 // ------------------------------------------------------------ wide node boxes
-// u8 frame decode: coordinate = fma(q, 2^e, origin), the device arithmetic.
+// u8 / u16 frame decode: coordinate = fma(q, 2^e, origin), the device arithmetic.
 SCION_HD float u8_decode(uint32_t q, float scale, float origin) { return fmaf((float)q, scale, origin); }
 
 // Write the W child boxes of a wide node (children 0..n-1 given as exact
 // boxes, padded here; slots n..W-1 and empty boxes are written as empty) and,
-// for u8, the node's frame header. Returns 0, or 2 (f16) / 4 (u8) when a code
+// for u8 / u16, the node's frame header. Returns 0, or 2 (f16) / 4 (u8, u16) when a code
 // could not enclose its box.
 SCION_HD int encode_wide_boxes(uint32_t W, uint32_t prec, uint32_t soa, const Box3 *exact, uint32_t n,
                                uint8_t *p) {
@@ -291,9 +291,10 @@ SCION_HD int encode_wide_boxes(uint32_t W, uint32_t prec, uint32_t soa, const Bo
       }
     return bad;
   }
-  // u8 relative to the merged child box (App. D.2), with a guard band of
-  // 2^-20 (|coordinate| + extent) beyond the padded boxes, power-of-two scale
-  // per axis, and verify-and-bump against the device decode.
+  // u8 / u16 codes relative to the merged child box (App. D.2), with a guard
+  // band of 2^-20 (|coordinate| + extent) beyond the padded boxes, a
+  // power-of-two scale per axis, and verify-and-bump against the device decode.
+  const uint32_t qmax = prec == PREC_U8 ? 255u : 65535u;
   double mlo[3], mhi[3];
   for (int a = 0; a < 3; ++a) {
     mlo[a] = INFINITY;
@@ -322,30 +323,36 @@ SCION_HD int encode_wide_boxes(uint32_t W, uint32_t prec, uint32_t soa, const Bo
     int e = -126;
     if (span > 0.0) {
       int ex;
-      frexp(span / 255.0, &ex);  // span/255 < 2^ex
+      frexp(span / (double)qmax, &ex);  // span/qmax < 2^ex
       e = ex - 2 > -126 ? ex - 2 : -126;
     }
-    while (e < 127 && ldexp(255.0, e) < span) ++e;
+    while (e < 127 && ldexp((double)qmax, e) < span) ++e;
     scale[a] = (float)ldexp(1.0, e);
     put_f32(p + 4 * a, origin[a]);
     p[12 + a] = (uint8_t)(e + 127);
   }
   for (uint32_t k = 0; k < W; ++k)
     for (int a = 0; a < 3; ++a) {
-      uint32_t qlo = 255, qhi = 0;
+      uint32_t qlo = qmax, qhi = 0;
       if (live[k]) {
         const double tlo = (double)cb[k].lo[a] - g, thi = (double)cb[k].hi[a] + g;
         const double fl = floor((tlo - origin[a]) / scale[a]);
         const double fh = ceil((thi - origin[a]) / scale[a]);
-        qlo = (uint32_t)fmin(255.0, fmax(0.0, fl));
-        qhi = (uint32_t)fmin(255.0, fmax(0.0, fh));
+        qlo = (uint32_t)fmin((double)qmax, fmax(0.0, fl));
+        qhi = (uint32_t)fmin((double)qmax, fmax(0.0, fh));
         while (qlo > 0 && (double)u8_decode(qlo, scale[a], origin[a]) > tlo) --qlo;
-        while (qhi < 255 && (double)u8_decode(qhi, scale[a], origin[a]) < thi) ++qhi;
+        while (qhi < qmax && (double)u8_decode(qhi, scale[a], origin[a]) < thi) ++qhi;
         if ((double)u8_decode(qlo, scale[a], origin[a]) > tlo || (double)u8_decode(qhi, scale[a], origin[a]) < thi)
           bad |= 4;
       }
-      p[wide_box_offset(W, prec, soa, k, a)] = (uint8_t)qlo;
-      p[wide_box_offset(W, prec, soa, k, 3 + a)] = (uint8_t)qhi;
+      uint8_t *plo = p + wide_box_offset(W, prec, soa, k, a), *phi = p + wide_box_offset(W, prec, soa, k, 3 + a);
+      if (prec == PREC_U8) {
+        *plo = (uint8_t)qlo;
+        *phi = (uint8_t)qhi;
+      } else {
+        put_u16(plo, (uint16_t)qlo);
+        put_u16(phi, (uint16_t)qhi);
+      }
     }
   return bad;
 }

@@ -195,7 +195,7 @@ __device__ __forceinline__ void cp_step_wide(const TraceArgs &a, CpLane &L, Stac
 #pragma unroll
   for (int i = 0; i < N::NQ; ++i) q[i] = ldg4(np + i);
   float ox = 0.f, oy = 0.f, oz = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-  if (PREC == PREC_U8) {
+  if (N::kGrid) {
     ox = __uint_as_float(q[0].x); oy = __uint_as_float(q[0].y); oz = __uint_as_float(q[0].z);
     sx = __uint_as_float((q[0].w & 0xFFu) << 23);
     sy = __uint_as_float(((q[0].w >> 8) & 0xFFu) << 23);

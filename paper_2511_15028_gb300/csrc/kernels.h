@@ -24,6 +24,9 @@ TraceKernel kernels_w4_p2(int soa, int cref, int any, int stats);
 TraceKernel kernels_w8_p0(int soa, int cref, int any, int stats);
 TraceKernel kernels_w8_p1(int soa, int cref, int any, int stats);
 TraceKernel kernels_w8_p2(int soa, int cref, int any, int stats);
+TraceKernel kernels_w2_p5(int soa, int cref, int any, int stats);
+TraceKernel kernels_w4_p5(int soa, int cref, int any, int stats);
+TraceKernel kernels_w8_p5(int soa, int cref, int any, int stats);
 // closest point query kernels of the same families
 TraceKernel cpq_kernels_own_p0(int soa, int cref, int stats);
 TraceKernel cpq_kernels_own_p3(int soa, int cref, int stats);
@@ -37,6 +40,9 @@ TraceKernel cpq_kernels_w4_p2(int soa, int cref, int stats);
 TraceKernel cpq_kernels_w8_p0(int soa, int cref, int stats);
 TraceKernel cpq_kernels_w8_p1(int soa, int cref, int stats);
 TraceKernel cpq_kernels_w8_p2(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w2_p5(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w4_p5(int soa, int cref, int stats);
+TraceKernel cpq_kernels_w8_p5(int soa, int cref, int stats);
 
 constexpr int kMaxThreadsPerBlock = 256;
 // Four 256-thread CTAs per SM: caps a traversal kernel at 64 registers so 32

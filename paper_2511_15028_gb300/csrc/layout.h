@@ -34,7 +34,9 @@
 //    Table 1, App. D.2). It holds the W child boxes and W child references:
 //      [header (u8 only, 16 B)] [boxes] [references], padded to 32 B.
 //      header : float3 origin (merged parent box, guard-expanded), 3 exponent
-//               bytes (biased by 127) and one spare byte.
+//               bytes (biased by 127) and one spare byte (u8 and u16 codes:
+//               coordinate = fma(code, 2^e, origin); the u16 form is the
+//               paper's bvh8-q16, App. D.2 with 16-bit codes).
 //      boxes  : 6 coordinates per child (lo.xyz, hi.xyz) of 4/2/1 bytes;
 //               AoS = per child, SoA = per coordinate across children.
 //      refs direct   : u32 per child (bit-stolen, App. D.2 "-ci" reading):
@@ -63,7 +65,7 @@
 
 namespace scion {
 
-enum BoxPrec : uint32_t { PREC_F32 = 0, PREC_F16 = 1, PREC_U8 = 2, PREC_Q16 = 3, PREC_EQ10 = 4 };
+enum BoxPrec : uint32_t { PREC_F32 = 0, PREC_F16 = 1, PREC_U8 = 2, PREC_Q16 = 3, PREC_EQ10 = 4, PREC_U16 = 5 };
 enum { LAYOUT_AOS = 0, LAYOUT_SOA = 1 };
 enum { REF_DIRECT = 0, REF_INDIRECT = 1 };
 enum { ORDER_DFS = 0, ORDER_BFS = 1, ORDER_TREELET = 2 };
@@ -87,8 +89,11 @@ SCION_HD uint32_t ref_leaf_count(uint32_t r) { return ((r >> 1) & 15u) + 1u; }
 constexpr uint32_t kMetaInterior = 0x80u;
 
 // ---- wide node geometry
-SCION_HD uint32_t prec_bytes(uint32_t prec) { return prec == PREC_F32 ? 4u : (prec == PREC_F16 ? 2u : 1u); }
-SCION_HD uint32_t wide_header_bytes(uint32_t prec) { return prec == PREC_U8 ? 16u : 0u; }
+// wide-node box element bytes: f32 4, f16 2, u8 1, u16 2
+SCION_HD uint32_t prec_bytes(uint32_t prec) { return prec == PREC_F32 ? 4u : (prec == PREC_U8 ? 1u : 2u); }
+// u8 / u16 codes are relative to a frame in the node header
+SCION_HD bool prec_is_parent_grid(uint32_t prec) { return prec == PREC_U8 || prec == PREC_U16; }
+SCION_HD uint32_t wide_header_bytes(uint32_t prec) { return prec_is_parent_grid(prec) ? 16u : 0u; }
 SCION_HD uint32_t wide_box_bytes(uint32_t W, uint32_t prec) { return W * 6u * prec_bytes(prec); }
 SCION_HD uint32_t wide_ref_bytes(uint32_t W, uint32_t cref) { return cref == REF_DIRECT ? 4u * W : 8u + W; }
 SCION_HD uint32_t wide_ref_offset(uint32_t W, uint32_t prec) {

@@ -283,8 +283,9 @@ __device__ __forceinline__ bool visit_leaf(const TraceArgs &a, const Ray &r, uin
 // ------------------------------------------------------------------ wide node
 template <int W, int PREC, int SOA, int CREF>
 struct WideNode {
-  static constexpr int kHdr = PREC == PREC_U8 ? 16 : 0;
-  static constexpr int kElem = PREC == PREC_F32 ? 4 : (PREC == PREC_F16 ? 2 : 1);
+  static constexpr bool kGrid = PREC == PREC_U8 || PREC == PREC_U16;  // codes on a node frame
+  static constexpr int kHdr = kGrid ? 16 : 0;
+  static constexpr int kElem = PREC == PREC_F32 ? 4 : (PREC == PREC_U8 ? 1 : 2);
   static constexpr int kRefOff = kHdr + W * 6 * kElem;
   static constexpr int kBytes = kRefOff + (CREF == REF_DIRECT ? 4 * W : 8 + W);
   static constexpr int kStride = (kBytes + 31) & ~31;
@@ -301,13 +302,16 @@ struct WideNode {
     if (kElem == 2) return (w >> ((off & 3) * 8)) & 0xFFFFu;
     return (w >> ((off & 3) * 8)) & 0xFFu;
   }
-  // u8 code of coordinate c of child k as a float, exactly: a byte permute
-  // puts the code into the low mantissa bits of 2^23, then 2^23 is taken off
-  // (full-rate integer/float ops instead of an integer-to-float conversion)
+  // u8 / u16 code of coordinate c of child k as a float, exactly: a byte
+  // permute puts the code into the low mantissa bits of 2^23, then 2^23 is
+  // taken off (full-rate integer/float ops instead of an integer-to-float
+  // conversion)
   static __device__ __forceinline__ float code(const uint4 (&q)[NQ], int k, int c) {
     const int off = box_off(k, c);
     const uint32_t w = qword(q, off >> 2);
-    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(off & 3))) - 8388608.0f;
+    const uint32_t b = (uint32_t)(off & 3);
+    const uint32_t sel = kElem == 1 ? (0x7540u | b) : (0x7400u | ((b + 1u) << 4) | b);
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.0f;
   }
 };
 
@@ -380,10 +384,10 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
     uint4 q[N::NQ];
 #pragma unroll
     for (int i = 0; i < N::NQ; ++i) q[i] = ldg4(np + i);
-    // u8 frame: coordinate = origin + code * 2^e, folded into the plane
+    // u8 / u16 frame: coordinate = origin + code * 2^e, folded into the plane
     // distance t = fma(code, 2^e / d, (origin - o) / d) per axis
     float ax = 0.f, bx = 0.f, ay = 0.f, by = 0.f, az = 0.f, bz = 0.f;
-    if (PREC == PREC_U8) {
+    if (N::kGrid) {
       ax = __uint_as_float((q[0].w & 0xFFu) << 23) * r.rx;
       ay = __uint_as_float(((q[0].w >> 8) & 0xFFu) << 23) * r.ry;
       az = __uint_as_float(((q[0].w >> 16) & 0xFFu) << 23) * r.rz;
@@ -412,7 +416,7 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
       }
       float tn;
       bool hit;
-      if (PREC == PREC_U8) {
+      if (N::kGrid) {
         const float lx = N::code(q, k, 0), ly = N::code(q, k, 1), lz = N::code(q, k, 2);
         const float hx = N::code(q, k, 3), hy = N::code(q, k, 4), hz = N::code(q, k, 5);
         const float nqx = r.nx ? hx : lx, fqx = r.nx ? lx : hx;

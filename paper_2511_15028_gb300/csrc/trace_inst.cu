@@ -1,6 +1,6 @@
 // Instantiates the traversal kernels of one node family. Compiled several
 // times with -DSCION_OWN=1 -DSCION_PREC=<0|3|4> (own-box node with f32, q16
-// or eq10 boxes), or -DSCION_W=<2|4|8> -DSCION_PREC=<0|1|2>, so the families
+// or eq10 boxes), or -DSCION_W=<2|4|8> -DSCION_PREC=<0|1|2|5>, so the families
 // build in parallel.
 #include "cpq.cuh"
 #include "kernels.h"

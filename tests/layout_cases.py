@@ -8,7 +8,7 @@ WORLD_GRID = ("q16", "eq10")
 def all_layouts():
     out = []
     for w, lay, prec, cref, pref, order in itertools.product(
-            (2, 4, 8), ("aos", "soa"), ("f32", "f16", "u8") + WORLD_GRID, ("direct", "indirect"),
+            (2, 4, 8), ("aos", "soa"), ("f32", "f16", "u8", "u16") + WORLD_GRID, ("direct", "indirect"),
             ("direct", "indirect"), ("dfs", "bfs", "treelet")):
         if prec in WORLD_GRID and (w != 2 or (prec == "eq10" and lay == "soa")):
             continue

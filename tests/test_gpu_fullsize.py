@@ -44,7 +44,7 @@ def test_config2_full_size_all_layouts(sc_mod, oracle_mod):
     hb = ob.closest(bounce)
     hs = ob.any(shadow)
     d = [torch.from_numpy(r).cuda() for r in (prim, bounce, shadow)]
-    for name, desc in scion.sweep_layouts(quantised_bvh2=True).items():
+    for name, desc in scion.sweep_layouts(extended=True).items():
         bvh = scion.scion_build(sc.verts, desc, sc.indices)
         _cmp(scion, scion.scion_trace_closest(bvh, d[0]), hp, name + " primary")
         _cmp(scion, scion.scion_trace_closest(bvh, d[1]), hb, name + " bounce")
@@ -68,7 +68,7 @@ def test_config3_full_size(sc_mod, oracle_mod):
     eocc = oracle_mod.any_brute(tris, short[pick])
     assert 0.3 < (exp["prim"] != 0xFFFFFFFF).mean() and 0.02 < eocc.mean() < 0.98
     d, ds = torch.from_numpy(rays).cuda(), torch.from_numpy(short).cuda()
-    for name, desc in scion.sweep_layouts(quantised_bvh2=True).items():
+    for name, desc in scion.sweep_layouts(extended=True).items():
         bvh = scion.scion_build(sc.verts, desc)
         got = scion.scion_trace_closest(bvh, d)[torch.from_numpy(pick).cuda()]
         _cmp(scion, got, exp, name + " closest")
@@ -116,7 +116,7 @@ def test_config2_full_size_closest_point(sc_mod, oracle_mod):
     pick = np.sort(rng.choice(pts.shape[0], 256, replace=False))
     exp = oracle_mod.cpq_brute(sc.triangles(), pts[pick])
     d = torch.from_numpy(pts).cuda()
-    for name, desc in scion.sweep_layouts(quantised_bvh2=True).items():
+    for name, desc in scion.sweep_layouts(extended=True).items():
         if name.endswith("indirect"):
             continue
         bvh = scion.scion_build(sc.verts, desc, sc.indices)

@@ -207,7 +207,7 @@ def test_config2_reduced_all_ray_kinds(sc_mod, oracle_mod):
     shadow = scenes.shadow_rays(sc, prim, h["t"], h["u"], h["v"], h["prim"])
     eb = ob.closest(bounce)
     es = ob.any(shadow)
-    for name, d in sc_mod.sweep_layouts(quantised_bvh2=True).items():
+    for name, d in sc_mod.sweep_layouts(extended=True).items():
         bvh = sc_mod.scion_build(sc.verts, d, sc.indices)
         assert_same_hits(gpu_closest(sc_mod, bvh, prim), h, name + " primary")
         assert_same_hits(gpu_closest(sc_mod, bvh, bounce), eb, name + " bounce")
@@ -225,7 +225,7 @@ def test_random_soup_incoherent(sc_mod, oracle_mod):
     ob = oracle_mod.BVH2(tris)
     exp = ob.closest(rays)
     eocc = ob.any(short)
-    for name, d in sc_mod.sweep_layouts(quantised_bvh2=True).items():
+    for name, d in sc_mod.sweep_layouts(extended=True).items():
         bvh = sc_mod.scion_build(verts, d)
         for p in (None, dict(rays_per_fetch=1), dict(rays_per_fetch=1, ordered_children=2, threads_per_block=128),
                   dict(ordered_children=3), dict(rays_per_fetch=1, ordered_children=3), dict(rays_per_fetch=8),

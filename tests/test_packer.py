@@ -103,7 +103,7 @@ def test_pbrt_node_size_and_wide_sizes():
     assert soa["node_bytes"] == 32 * soa["n_nodes"]  # pbrt-soaos: still 32 B per node
     expect = {(4, "f32", "direct"): 128, (8, "f16", "direct"): 128, (8, "u8", "direct"): 96,
               (8, "u8", "indirect"): 96, (8, "f32", "direct"): 224, (4, "u8", "direct"): 64,
-              (2, "f16", "direct"): 32}
+              (2, "f16", "direct"): 32, (8, "u16", "direct"): 160, (4, "u16", "indirect"): 96}
     for (w, p, c), size in expect.items():
         i = scion.scion_debug_build_host(sc.verts, scion.layout(width=w, box_prec=p, child_ref=c), sc.indices).info
         assert i["node_stride"] == size, (w, p, c)
@@ -125,7 +125,7 @@ def test_soup_extreme_coordinates_enclosure():
         v = scenes.random_soup(rng, 3000, mu=math.log(0.01)) * scale + offset
         v = v.astype(np.float32)
         tris = v.reshape(-1, 9)
-        for prec in ("f32", "f16", "u8") + WORLD_GRID:
+        for prec in ("f32", "f16", "u8", "u16") + WORLD_GRID:
             for w in ((2,) if prec in WORLD_GRID else (2, 4, 8)):
                 dec = scion.scion_debug_build_host(v, scion.layout(width=w, box_prec=prec))
                 sub, leaves = walk(dec)
@@ -175,7 +175,7 @@ def test_nonfinite_triangles_left_out_and_empty_scene():
 
 def test_invalid_descriptors_rejected():
     v = scenes.config1_scene().triangles().reshape(-1, 3)
-    bad = [dict(width=3), dict(width=16), dict(box_prec=5), dict(order=3), dict(leaf_max=17),
+    bad = [dict(width=3), dict(width=16), dict(box_prec=6), dict(order=3), dict(leaf_max=17),
            dict(sah_bins=1), dict(sah_bins=65), dict(align=1), dict(align=32),
            dict(width=4, box_prec=3), dict(width=8, box_prec=4), dict(box_prec=3, leaf_max=16),
            dict(box_prec=4, box_layout=1), dict(width=2, box_prec=3, child_ref=0, order=1),
