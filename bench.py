@@ -55,6 +55,8 @@ def node_load_bytes(desc) -> int:
         return 16
     if prec == 4:  # eq10 own-box node: 12 B (16 B aligned)
         return 16 if desc.align == 16 else 12
+    if prec == 6:  # shared-slab node: planes + field + meta
+        return 16
     elem = {0: 4, 1: 2, 2: 1, 5: 2}[prec]
     used = (16 if prec in (2, 5) else 0) + w * 6 * elem + (4 * w if cref == 0 else 8 + w)
     return (used + 15) // 16 * 16
@@ -450,7 +452,7 @@ def bench_cpq(scion, torch, steps, warmup, hbm_peak):
     out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
     res = {}
     for name, desc in scion.sweep_layouts(extended=True).items():
-        if name.endswith("indirect"):
+        if name.endswith("indirect") or name.startswith("bvh2_slab"):  # slab: rays only
             continue
         bvh = scion.scion_build(sc.verts, desc, sc.indices)
         _, c = scion.scion_trace_stats(bvh, pts, 2)

@@ -71,6 +71,14 @@ typedef enum {
  *               These need leaf_max <= 15 and fewer than 2^26 nodes; q16
  *               takes AoS or SoA ("-soaos": code array + word array), eq10
  *               AoS only.
+ *               5 u16: children-in-parent codes relative to the parent's
+ *               merged box like u8, 16 bits each (bvh8-q16 of Table 1).
+ *               6 shared slab (Section 8.3): width-2 node without a box: the
+ *               split axis and two planes (the left child's upper and the
+ *               right child's lower bound on that axis), 16 B; children
+ *               inherit the other planes from the parent's box, which the
+ *               traversal carries from the root. AoS only; not for closest
+ *               point queries (SCION_ERR_UNSUPPORTED_LAYOUT there).
  *  child_ref  : 0 direct (an explicit reference per child; for the width-2
  *               own-box node: implicit left = I+1 and stored right offset,
  *               which requires order = DFS), 1 indirect (one base index,
@@ -212,8 +220,9 @@ scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint3
  *  d_verts : float [n_verts][3], DEVICE memory; n_verts must equal the
  *            BVH's vertex count.
  *  stream  : the refit kernels run on it, asynchronously, except for the
- *            world-grid layouts (q16, eq10), whose new grid is read back
- *            (the call then synchronises the stream).
+ *            world-grid layouts (q16, eq10) and the shared-slab layout,
+ *            whose new grid or root box is read back (the call then
+ *            synchronises the stream).
  * No trace of this BVH may run concurrently on another stream. The first
  * call allocates about 32 bytes of device scratch per node, kept until
  * scion_destroy. A box code that cannot enclose its box sets the device

@@ -26,7 +26,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "--fmad=false", "-prec-div=true", "-prec-sqrt
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
              "-Wall", "-I", INCLUDE]
 
-FAMILIES = [(f"own_p{p}", ["-DSCION_OWN=1", f"-DSCION_PREC={p}"]) for p in (0, 3, 4)] + [
+FAMILIES = [(f"own_p{p}", ["-DSCION_OWN=1", f"-DSCION_PREC={p}"]) for p in (0, 3, 4, 6)] + [
     (f"w{w}_p{p}", [f"-DSCION_W={w}", f"-DSCION_PREC={p}"]) for w in (2, 4, 8) for p in (0, 1, 2, 5)]
 
 

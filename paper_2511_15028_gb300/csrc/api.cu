@@ -129,8 +129,19 @@ void bvh_args(const scion_bvh b, TraceArgs &a) {
   for (int k = 0; k < 9; ++k) a.frame[k] = b->frame[k];
 }
 
+// Dynamic shared memory above this needs the kernel's opt-in attribute (the
+// default limit of 48 KB also covers the kernels' static shared memory).
+constexpr size_t kSmemOptIn = 32 * 1024;
+
 // Query kinds of launch_trace.
 constexpr int kQueryClosest = 0, kQueryAny = 1, kQueryPoint = 2;
+
+// Shared-memory stack bytes per entry: (ref, entry distance), plus the exit
+// distance for the shared-slab layout, whose traversal carries intervals.
+size_t stack_entry_bytes(const scion_bvh b, int query) {
+  const bool slab = b->own_box && b->desc.box_prec == PREC_SLAB && query != kQueryPoint;
+  return sizeof(uint2) + (slab ? sizeof(float) : 0);
+}
 
 TraceKernel pick_cpq_kernel(const scion_bvh b, int stats) {
   const scion_layout_desc &d = b->desc;
@@ -140,6 +151,7 @@ TraceKernel pick_cpq_kernel(const scion_bvh b, int stats) {
       case PREC_F32: return cpq_kernels_own_p0(soa, cref, stats);
       case PREC_Q16: return cpq_kernels_own_p3(soa, cref, stats);
       case PREC_EQ10: return cpq_kernels_own_p4(soa, cref, stats);
+      case PREC_SLAB: return cpq_kernels_own_p6(soa, cref, stats);
     }
     return nullptr;
   }
@@ -170,6 +182,7 @@ TraceKernel pick_kernel(const scion_bvh b, int query, int stats) {
       case PREC_F32: return kernels_own_p0(soa, cref, any, stats);
       case PREC_Q16: return kernels_own_p3(soa, cref, any, stats);
       case PREC_EQ10: return kernels_own_p4(soa, cref, any, stats);
+      case PREC_SLAB: return kernels_own_p6(soa, cref, any, stats);
     }
     return nullptr;
   }
@@ -319,7 +332,7 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   const uint32_t ordered = order_mode(p.ordered_children);
   TraceKernel k = pick_kernel(b, query, stats ? 1 : 0);
   if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
-  const size_t smem = (size_t)tpb * smem_entries * sizeof(uint2);
+  const size_t smem = (size_t)tpb * smem_entries * stack_entry_bytes(b, query);
   int dev = 0;
   cudaGetDevice(&dev);
   uint32_t ctas = p.ctas_per_sm;
@@ -328,7 +341,7 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
     SCION_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k, (int)tpb, smem));
     ctas = (uint32_t)std::max(nb, 1);
   }
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     SCION_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
   TraceArgs a;
@@ -560,7 +573,7 @@ scion_status scion_refit(scion_bvh bvh, const float *d_verts, uint64_t n_verts, 
   rb.frame = b->d_refit_frame;
   rb.status = b->d_scratch + 3;
   SCION_CUDA(refit_launch(rb, d_verts, s));
-  if (prec_is_world_grid(b->desc.box_prec) && b->n_nodes > 0) {
+  if (prec_has_frame(b->desc.box_prec) && b->n_nodes > 0) {
     // the traversal takes the grid as a launch argument: read it back
     SCION_CUDA(cudaMemcpyAsync(b->frame, b->d_refit_frame, 9 * sizeof(float), cudaMemcpyDeviceToHost, s));
     SCION_CUDA(cudaStreamSynchronize(s));
@@ -886,6 +899,23 @@ scion_status scion_debug_host_decode(scion_host_bvh h, uint32_t *kind, uint32_t 
       own_boxes[(size_t)i * 6 + 3 + q] = own.hi[q];
     }
   }
+  if (hb.desc.box_prec == PREC_SLAB && hb.n_nodes > 0) {
+    // carried boxes top-down (parents precede children in every node order):
+    // the root's is the frame, a child's is its parent's with one plane moved
+    for (int q = 0; q < 6; ++q) own_boxes[q] = hb.frame[q];
+    for (uint32_t i = 0; i < hb.n_nodes; ++i) {
+      if (kind[(size_t)i * 8] != 1) continue;
+      const uint8_t *p = hb.nodes.data() + (size_t)i * kSlabNodeBytes;
+      const uint32_t ax = bin_meta_axis(get_u32(p + 12));
+      const uint32_t l = a[(size_t)i * 8], r = a[(size_t)i * 8 + 1];
+      for (int q = 0; q < 6; ++q) {
+        own_boxes[(size_t)l * 6 + q] = own_boxes[(size_t)i * 6 + q];
+        own_boxes[(size_t)r * 6 + q] = own_boxes[(size_t)i * 6 + q];
+      }
+      own_boxes[(size_t)l * 6 + 3 + ax] = get_f32(p);
+      own_boxes[(size_t)r * 6 + ax] = get_f32(p + 4);
+    }
+  }
   for (uint32_t i = 0; i < hb.n_leaf_entries; ++i) {
     if (hb.desc.prim_ref == REF_DIRECT) std::memcpy(&leaf_ids[i], &hb.prim_direct[(size_t)i * 12 + 3], 4);
     else leaf_ids[i] = hb.prim_ids[i];
@@ -984,7 +1014,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // the counters must start at zero; they keep the previous call's values
   SCION_CUDA(cudaMemsetAsync(scratch, 0, kStaticScratchUsed, s));
-  const size_t smem = (size_t)tpb * smem_entries * sizeof(uint2);
+  const size_t smem = (size_t)tpb * smem_entries * stack_entry_bytes(b, kQueryClosest);
   int dev = 0;
   cudaGetDevice(&dev);
   uint32_t ctas = p.ctas_per_sm;
@@ -993,7 +1023,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
     SCION_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k, (int)tpb, smem));
     ctas = (uint32_t)std::max(nb, 1);
   }
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     SCION_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
   TraceArgs a;

@@ -20,7 +20,7 @@ scion_status normalize_desc(const scion_layout_desc &in, scion_layout_desc *out,
   scion_layout_desc d = in;
   if (d.align != 0 && d.align != 16) return SCION_ERR_INVALID_ARG;
   if (d.width != 2 && d.width != 4 && d.width != 8) return SCION_ERR_UNSUPPORTED_LAYOUT;
-  if (d.box_layout > 1 || d.box_prec > PREC_U16 || d.child_ref > 1 || d.prim_ref > 1 || d.order > 2)
+  if (d.box_layout > 1 || d.box_prec > PREC_SLAB || d.child_ref > 1 || d.prim_ref > 1 || d.order > 2)
     return SCION_ERR_UNSUPPORTED_LAYOUT;
   if (d.leaf_max == 0) d.leaf_max = 4;
   if (d.leaf_max > kMaxLeaf) return SCION_ERR_UNSUPPORTED_LAYOUT;
@@ -31,7 +31,9 @@ scion_status normalize_desc(const scion_layout_desc &in, scion_layout_desc *out,
     if (d.width != 2 || d.leaf_max > kQMaxLeaf) return SCION_ERR_UNSUPPORTED_LAYOUT;
     if (d.box_prec == PREC_EQ10 && d.box_layout == LAYOUT_SOA) return SCION_ERR_UNSUPPORTED_LAYOUT;
   }
-  const bool ob = d.width == 2 && (d.box_prec == PREC_F32 || prec_is_world_grid(d.box_prec));
+  if (d.box_prec == PREC_SLAB && (d.width != 2 || d.box_layout != LAYOUT_AOS)) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  const bool ob = d.width == 2 && (d.box_prec == PREC_F32 || prec_is_world_grid(d.box_prec) ||
+                                   d.box_prec == PREC_SLAB);
   if (ob && d.child_ref == REF_DIRECT && d.order != ORDER_DFS) return SCION_ERR_UNSUPPORTED_LAYOUT;
   *out = d;
   *own_box = ob;
@@ -603,7 +605,9 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
       return SCION_ERR_UNSUPPORTED_LAYOUT;
     }
     uint32_t ref_bytes = 0;  // SoA word/ref array element
-    if (!quant) {
+    if (prec == PREC_SLAB) {
+      out->node_stride = kSlabNodeBytes;
+    } else if (!quant) {
       out->node_stride = soa ? (a16 ? 32u : kBinBoxBytes) : kBinNodeBytes;
       ref_bytes = soa ? kBinRefBytes : 0u;
     } else if (prec == PREC_Q16) {
@@ -617,6 +621,45 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
     // world grid over the padded root box: q16 {wlo, step}, eq10 {wlo, whi, bin}
     float bins_inv[3] = {0.f, 0.f, 0.f};
     if (quant) world_frame(prec, padded(lb.nodes[0].box), out->frame, bins_inv);
+    // shared slab: the plane axis of each node is the one whose two carried
+    // child boxes have the least total surface area (the boxes the traversal
+    // tests); carried boxes top-down from the padded root box
+    std::vector<uint8_t> slab_axis;
+    if (prec == PREC_SLAB) {
+      const Box3 root = padded(lb.nodes[0].box);
+      for (int a = 0; a < 3; ++a) {
+        out->frame[a] = root.lo[a];
+        out->frame[3 + a] = root.hi[a];
+      }
+      slab_axis.assign(nl, 0);
+      std::vector<std::pair<uint32_t, Box3>> todo{{0u, root}};
+      while (!todo.empty()) {
+        const uint32_t x = todo.back().first;
+        const Box3 cx = todo.back().second;
+        todo.pop_back();
+        const LNode &nd = lb.nodes[x];
+        if (nd.count > 0) continue;
+        const Box3 pl = padded(lb.nodes[nd.left].box), pr = padded(lb.nodes[nd.right].box);
+        int best = (int)nd.axis;
+        double best_cost = INFINITY;
+        Box3 bl = cx, br = cx;
+        for (int a = 0; a < 3; ++a) {
+          Box3 l = cx, r = cx;
+          l.hi[a] = pl.hi[a];
+          r.lo[a] = pr.lo[a];
+          const double cost = box_area(l) + box_area(r);
+          if (cost < best_cost) {
+            best_cost = cost;
+            best = a;
+            bl = l;
+            br = r;
+          }
+        }
+        slab_axis[x] = (uint8_t)best;
+        todo.push_back({nd.left, bl});
+        todo.push_back({nd.right, br});
+      }
+    }
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (long long pi = 0; pi < (long long)nl; ++pi) {
@@ -638,6 +681,16 @@ scion_status pack_bvh(const BuildInput &in, const LogicalBVH &lb, const scion_la
         meta = bin_pack_meta(0, nd.axis);
       }
       uint8_t *p = out->nodes.data() + pi * out->node_stride;
+      if (prec == PREC_SLAB) {
+        if (nd.count == 0) {
+          const uint32_t ax = slab_axis[ord[pi]];
+          encode_slab_planes(lb.nodes[nd.left].box, lb.nodes[nd.right].box, ax, p);
+          meta = bin_pack_meta(0, ax);
+        }
+        put_u32(p + 8, ref);
+        put_u32(p + 12, meta);
+        continue;
+      }
       bad |= encode_own_box(prec, nd.box, out->frame, bins_inv, p) ? 0 : 2;
       if (!quant) {
         uint8_t *q = soa ? out->nodes2.data() + pi * kBinRefBytes : p + 24;
@@ -802,7 +855,12 @@ int decode_node(const HostBVH &b, uint32_t node, DecodedChild *ch, Box3 *own) {
     const bool soa = d.box_layout == LAYOUT_SOA;
     const uint8_t *p = b.nodes.data() + (size_t)node * b.node_stride;
     uint32_t ref, cnt;
-    if (d.box_prec == PREC_F32) {
+    if (d.box_prec == PREC_SLAB) {
+      // the carried box depends on the ancestors: left to the caller
+      for (int a = 0; a < 3; ++a) own->lo[a] = own->hi[a] = NAN;
+      ref = get_u32(p + 8);
+      cnt = bin_meta_count(get_u32(p + 12));
+    } else if (d.box_prec == PREC_F32) {
       const uint8_t *q = soa ? b.nodes2.data() + (size_t)node * kBinRefBytes : p + 24;
       for (int a = 0; a < 3; ++a) {
         own->lo[a] = get_f32(p + 4 * a);

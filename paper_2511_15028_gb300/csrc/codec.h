@@ -250,6 +250,18 @@ SCION_HD bool encode_own_box(uint32_t prec, const Box3 &exact, const float *fram
   return ok;
 }
 
+// ------------------------------------------------------------ shared-slab node
+// Split planes of a shared-slab node from its children's exact boxes: the
+// left child keeps the node's carried box with hi[axis] = slo, the right one
+// with lo[axis] = shi; slo and shi are the padded children's planes, so each
+// child's carried box encloses its padded box (the node's carried box already
+// encloses the node's padded box, and a child's pad is at most its parent's).
+SCION_HD void encode_slab_planes(const Box3 &left_exact, const Box3 &right_exact, uint32_t axis, uint8_t *p) {
+  const bool le = box_is_empty(left_exact), re = box_is_empty(right_exact);
+  put_f32(p, le ? -INFINITY : padded(left_exact).hi[axis]);
+  put_f32(p + 4, re ? INFINITY : padded(right_exact).lo[axis]);
+}
+
 // ------------------------------------------------------------ wide node boxes
 // u8 / u16 frame decode: coordinate = fma(q, 2^e, origin), the device arithmetic.
 SCION_HD float u8_decode(uint32_t q, float scale, float origin) { return fmaf((float)q, scale, origin); }

@@ -9,12 +9,13 @@ typedef void (*TraceKernel)(TraceArgs);
 
 // Defined by trace_inst.cu, compiled once per node family:
 //   own-box binary node       : kernels_own_p<prec>(soa, cref, any, stats),
-//                               prec 0 f32, 3 q16, 4 eq10
+//                               prec 0 f32, 3 q16, 4 eq10, 6 shared slab
 //   wide node of width W, prec: kernels_w<W>_p<prec>(soa, cref, any, stats)
 // stats = 1 selects the counting variant (visit counters, same results).
 TraceKernel kernels_own_p0(int soa, int cref, int any, int stats);
 TraceKernel kernels_own_p3(int soa, int cref, int any, int stats);
 TraceKernel kernels_own_p4(int soa, int cref, int any, int stats);
+TraceKernel kernels_own_p6(int soa, int cref, int any, int stats);
 TraceKernel kernels_w2_p0(int soa, int cref, int any, int stats);
 TraceKernel kernels_w2_p1(int soa, int cref, int any, int stats);
 TraceKernel kernels_w2_p2(int soa, int cref, int any, int stats);
@@ -31,6 +32,7 @@ TraceKernel kernels_w8_p5(int soa, int cref, int any, int stats);
 TraceKernel cpq_kernels_own_p0(int soa, int cref, int stats);
 TraceKernel cpq_kernels_own_p3(int soa, int cref, int stats);
 TraceKernel cpq_kernels_own_p4(int soa, int cref, int stats);
+TraceKernel cpq_kernels_own_p6(int soa, int cref, int stats);  // null: not supported
 TraceKernel cpq_kernels_w2_p0(int soa, int cref, int stats);
 TraceKernel cpq_kernels_w2_p1(int soa, int cref, int stats);
 TraceKernel cpq_kernels_w2_p2(int soa, int cref, int stats);

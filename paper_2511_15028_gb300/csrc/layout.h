@@ -23,6 +23,8 @@
 //      q16  ("sg-pbrt-q16"): 6 x u16 codes (lo.xyz, hi.xyz) + word = 16 B;
 //           coordinate = fma(code, step[a], wlo[a]) (one rounding).
 //           SoA ("-soaos"): 12 B code array (16 B with align 16) + u32 words.
+//      (the shared-slab node of Section 8.3 is a third own-box-like binary
+//      node: see kSlabNodeBytes below)
 //      eq10 ("sg-eq"): u32 lo codes (x << 20 | y << 10 | z, counted up from
 //           wlo), u32 hi codes (same packing, counted down from whi), word =
 //           12 B (16 B with align 16); lo = rd(code * bin + wlo),
@@ -65,7 +67,9 @@
 
 namespace scion {
 
-enum BoxPrec : uint32_t { PREC_F32 = 0, PREC_F16 = 1, PREC_U8 = 2, PREC_Q16 = 3, PREC_EQ10 = 4, PREC_U16 = 5 };
+enum BoxPrec : uint32_t {
+  PREC_F32 = 0, PREC_F16 = 1, PREC_U8 = 2, PREC_Q16 = 3, PREC_EQ10 = 4, PREC_U16 = 5, PREC_SLAB = 6
+};
 enum { LAYOUT_AOS = 0, LAYOUT_SOA = 1 };
 enum { REF_DIRECT = 0, REF_INDIRECT = 1 };
 enum { ORDER_DFS = 0, ORDER_BFS = 1, ORDER_TREELET = 2 };
@@ -135,6 +139,16 @@ SCION_HD uint32_t qbin_first(uint32_t w) { return w >> 4; }
 SCION_HD uint32_t eq10_pack(uint32_t x, uint32_t y, uint32_t z) { return (x << 20) | (y << 10) | z; }
 SCION_HD uint32_t eq10_code(uint32_t w, int axis) { return (w >> (20 - 10 * axis)) & 1023u; }
 SCION_HD bool prec_is_world_grid(uint32_t prec) { return prec == PREC_Q16 || prec == PREC_EQ10; }
+// layouts whose traversal takes per-BVH constants (frame) as launch arguments
+SCION_HD bool prec_has_frame(uint32_t prec) { return prec_is_world_grid(prec) || prec == PREC_SLAB; }
+
+// ---- shared-slab binary node (Section 8.3, tree-carried bounds)
+// 16 B: f32 slo, f32 shi, u32 field, u32 meta (bin_pack_meta: count | axis << 16).
+// Interior: the left child's box is the node's carried box with hi[axis] =
+// slo, the right child's with lo[axis] = shi; the root's carried box is the
+// frame (padded root box). field: right offset (direct) or left index
+// (indirect); leaf: first prim.
+constexpr uint32_t kSlabNodeBytes = 16;
 
 constexpr uint32_t kPrimDirectBytes = 48;
 

@@ -89,7 +89,10 @@ __device__ int node_slots(const Tree &t, uint32_t x, Slot *s) {
   const uint8_t *p = t.nodes + (size_t)x * t.stride;
   if (t.own) {
     uint32_t cnt, field;
-    if (t.prec == PREC_F32) {
+    if (t.prec == PREC_SLAB) {
+      field = get_u32(p + 8);
+      cnt = bin_meta_count(get_u32(p + 12));
+    } else if (t.prec == PREC_F32) {
       const uint8_t *q = t.soa ? t.nodes2 + (size_t)x * kBinRefBytes : p + 24;
       field = get_u32(q);
       cnt = bin_meta_count(get_u32(q + 4));
@@ -203,8 +206,16 @@ __global__ void frame_kernel(Tree t, const Box3 *boxes, float *frame) {
   Box3 r = load_box(boxes, 0);
   if (box_is_empty(r))
     for (int a = 0; a < 3; ++a) r.lo[a] = r.hi[a] = 0.0f;
+  const Box3 pr = padded(r);
+  if (t.prec == PREC_SLAB) {  // the root's carried box
+    for (int a = 0; a < 3; ++a) {
+      frame[a] = pr.lo[a];
+      frame[3 + a] = pr.hi[a];
+    }
+    return;
+  }
   float bins_inv[3];
-  world_frame(t.prec, padded(r), frame, bins_inv);
+  world_frame(t.prec, pr, frame, bins_inv);
   for (int a = 0; a < 3; ++a) frame[9 + a] = bins_inv[a];
 }
 
@@ -213,8 +224,13 @@ __global__ void encode_kernel(Tree t, const Box3 *boxes, const float *frame, uin
   for (int k = 0; k < 12; ++k) fr[k] = frame ? frame[k] : 0.f;
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < t.n_nodes; x += gridDim.x * blockDim.x) {
     uint8_t *p = t.nodes + (size_t)x * t.stride;
-    bool ok;
-    if (t.own) {
+    bool ok = true;
+    if (t.own && t.prec == PREC_SLAB) {
+      Slot s[8];
+      node_slots(t, x, s);
+      if (s[0].kind == 1)
+        encode_slab_planes(load_box(boxes, s[0].node), load_box(boxes, s[1].node), bin_meta_axis(get_u32(p + 12)), p);
+    } else if (t.own) {
       ok = encode_own_box(t.prec, load_box(boxes, x), fr, fr + 9, p);
     } else {
       Slot s[8];
@@ -259,7 +275,7 @@ cudaError_t refit_launch(const RefitBuffers &b, const float *d_new_verts, cudaSt
   if (e != cudaSuccess) return e;
   links_kernel<<<grid_for(b.n_nodes), 256, 0, s>>>(t, b.parent, b.pending);
   boxes_kernel<<<grid_for(b.n_nodes), 256, 0, s>>>(t, b.parent, b.pending, reinterpret_cast<Box3 *>(b.boxes));
-  const bool grid = prec_is_world_grid(t.prec);
+  const bool grid = prec_has_frame(t.prec);
   if (grid) frame_kernel<<<1, 32, 0, s>>>(t, reinterpret_cast<const Box3 *>(b.boxes), b.frame);
   encode_kernel<<<grid_for(b.n_nodes), 256, 0, s>>>(t, reinterpret_cast<const Box3 *>(b.boxes),
                                                     grid ? b.frame : nullptr, b.status);

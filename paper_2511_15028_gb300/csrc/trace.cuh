@@ -147,6 +147,17 @@ __device__ __forceinline__ bool slab(const Ray &r, float lox, float loy, float l
                 fmaf(fx, r.rx, -r.orx), fmaf(fy, r.ry, -r.ory), fmaf(fz, r.rz, -r.orz), tlim, tn);
 }
 
+// The conservative ray interval [tn, tf] of a box, clamped to [tmin, tlim].
+__device__ __forceinline__ bool slab_interval(const Ray &r, float lox, float loy, float loz, float hix,
+                                              float hiy, float hiz, float tlim, float &tn, float &tf) {
+  const float nx = r.nx ? hix : lox, fx = r.nx ? lox : hix;
+  const float ny = r.ny ? hiy : loy, fy = r.ny ? loy : hiy;
+  const float nz = r.nz ? hiz : loz, fz = r.nz ? loz : hiz;
+  tn = fmaxf(fmax3(fmaf(nx, r.rx, -r.orx), fmaf(ny, r.ry, -r.ory), fmaf(nz, r.rz, -r.orz)) * kNearScale, r.tmin);
+  tf = fminf(fmin3(fmaf(fx, r.rx, -r.orx), fmaf(fy, r.ry, -r.ory), fmaf(fz, r.rz, -r.orz)) * kFarScale, tlim);
+  return tn <= tf;
+}
+
 // Pinned watertight ray/triangle test (Woop, Benthin & Wald, JCGT 2(1) 2013;
 // the paper's App. G uses Moller-Trumbore instead). Steps and rounding:
 //   A = p0 - o, B = p1 - o, C = p2 - o; sheared Ax = fma(-Sx, A[kz], A[kx]),
@@ -210,26 +221,45 @@ __device__ __forceinline__ uint32_t qword(const uint4 (&q)[NQ], int i) {
 }
 
 // ------------------------------------------------------------------ stack
-struct Stack {
+// Entries (ref, entry distance); with TF also the exit distance of the
+// entry's interval (the shared-slab traversal carries intervals, not boxes),
+// in a second shared-memory column.
+template <bool TF>
+struct StackT {
   uint2 *sh;      // this thread's column in shared memory
+  float *shf;     // exit distances (TF)
   int stride;     // blockDim.x
   int cap_sh;     // entries in shared memory
   int sp;
+  float ptf;      // exit distance of the last popped entry (TF)
   uint2 loc[kLocalStack];
+  float locf[TF ? kLocalStack : 1];
 
-  __device__ __forceinline__ bool push(uint32_t ref, float tn) {
+  __device__ __forceinline__ bool push(uint32_t ref, float tn, float tf = 0.f) {
     const uint2 e = make_uint2(ref, __float_as_uint(tn));
-    if (sp < cap_sh) sh[sp * stride] = e;
-    else if (sp < cap_sh + kLocalStack) loc[sp - cap_sh] = e;
-    else return false;
+    if (sp < cap_sh) {
+      sh[sp * stride] = e;
+      if (TF) shf[sp * stride] = tf;
+    } else if (sp < cap_sh + kLocalStack) {
+      loc[sp - cap_sh] = e;
+      if (TF) locf[sp - cap_sh] = tf;
+    } else {
+      return false;
+    }
     ++sp;
     return true;
   }
   __device__ __forceinline__ uint2 pop() {
     --sp;
-    return sp < cap_sh ? sh[sp * stride] : loc[sp - cap_sh];
+    if (sp < cap_sh) {
+      if (TF) ptf = shf[sp * stride];
+      return sh[sp * stride];
+    }
+    if (TF) ptf = locf[sp - cap_sh];
+    return loc[sp - cap_sh];
   }
 };
+using Stack = StackT<false>;
 
 // ------------------------------------------------------------------ leaf
 struct Best {
@@ -321,6 +351,7 @@ struct Lane {
   Ray r;
   Best b;
   uint32_t cur;      // entry being processed (kEmptyRef: ray finished)
+  float ctn, ctf;    // shared-slab layout: the current node's ray interval
   uint32_t steps;
   uint32_t err;
   bool found;        // any-hit result
@@ -573,25 +604,121 @@ __device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, Stack &st,
   L.cur = st.sp > 0 ? st.pop().x : kEmptyRef;
 }
 
+// Shared-slab binary node (Section 8.3): the node's box is not stored; the
+// lane carries the ray interval of the current node's box, and a child's
+// interval is that interval clipped by the one plane the child moves (slo:
+// the left child's upper bound on the split axis, shi: the right child's
+// lower bound), widened like every slab distance. Stacked entries keep their
+// interval.
+template <bool ANY>
+__device__ __forceinline__ void slab_pop(Lane &L, StackT<true> &st) {
+  while (st.sp > 0) {
+    const uint2 e = st.pop();
+    const float tn = __uint_as_float(e.y);
+    if (ANY || tn <= L.b.t) {
+      L.cur = e.x;
+      L.ctn = tn;
+      L.ctf = st.ptf;
+      return;
+    }
+  }
+  L.cur = kEmptyRef;
+}
+
+template <int CREF, bool ANY, bool STATS>
+__device__ __forceinline__ void step_slab(const TraceArgs &a, Lane &L, StackT<true> &st, Counts &cnt) {
+  const Ray &r = L.r;
+  const uint32_t cur = L.cur;
+  if (STATS) cnt.nodes++;
+  const uint4 v = ldg4(a.nodes + cur);
+  const uint32_t n = bin_meta_count(v.w);
+  if (n > 0) {
+    if (visit_leaf<ANY, STATS>(a, r, v.z, n, L.b, cnt)) {
+      L.found = true;
+      L.cur = kEmptyRef;
+      return;
+    }
+    slab_pop<ANY>(L, st);
+    return;
+  }
+  const uint32_t ax = bin_meta_axis(v.w);
+  const float rd = ax == 0 ? r.rx : (ax == 1 ? r.ry : r.rz);
+  const float od = ax == 0 ? r.orx : (ax == 1 ? r.ory : r.orz);
+  const bool neg = ax == 0 ? r.nx : (ax == 1 ? r.ny : r.nz);
+  const float tlo = fmaf(__uint_as_float(v.x), rd, -od), thi = fmaf(__uint_as_float(v.y), rd, -od);
+  const float tf = fminf(L.ctf, ANY ? r.tmax : fminf(r.tmax, L.b.t));
+  float ln = L.ctn, lf = tf, rn = L.ctn, rf = tf;
+  if (!neg) {
+    lf = fminf(lf, tlo * kFarScale);   // left: coordinate <= slo, reached before tlo
+    rn = fmaxf(rn, thi * kNearScale);  // right: coordinate >= shi, reached after thi
+  } else {
+    ln = fmaxf(ln, tlo * kNearScale);
+    rf = fminf(rf, thi * kFarScale);
+  }
+  const bool hl = ln <= lf, hr = rn <= rf;
+  const uint32_t l = CREF == REF_DIRECT ? cur + 1 : v.z, rc = CREF == REF_DIRECT ? cur + v.z : v.z + 1;
+  if (hl && hr) {
+    const bool right_first = !ANY && a.ordered && rn < ln;
+    const bool ok = right_first ? st.push(l, ln, lf) : st.push(rc, rn, rf);
+    if (!ok) { L.err = kErrStack; L.cur = kEmptyRef; return; }
+    L.cur = right_first ? rc : l;
+    L.ctn = right_first ? rn : ln;
+    L.ctf = right_first ? rf : lf;
+  } else if (hl) {
+    L.cur = l; L.ctn = ln; L.ctf = lf;
+  } else if (hr) {
+    L.cur = rc; L.ctn = rn; L.ctf = rf;
+  } else {
+    slab_pop<ANY>(L, st);
+  }
+}
+
+// First entry of a ray: the root (own-box and wide nodes), or for the
+// shared-slab layout the root with the ray interval of the frame box.
+template <bool OWN, int PREC>
+__device__ __forceinline__ void start_ray(const TraceArgs &a, Lane &L) {
+  if constexpr (OWN && PREC == PREC_SLAB) {
+    float tn, tf;
+    const bool in = a.n_nodes > 0 && slab_interval(L.r, a.frame[0], a.frame[1], a.frame[2], a.frame[3], a.frame[4],
+                                                   a.frame[5], L.r.tmax, tn, tf);
+    L.cur = in ? 0u : kEmptyRef;
+    L.ctn = tn;
+    L.ctf = tf;
+  } else if constexpr (OWN) {
+    L.cur = a.n_nodes > 0 ? 0u : kEmptyRef;
+  } else {
+    L.cur = a.root_ref;
+  }
+}
+
+template <bool OWN, int PREC>
+using StackFor = StackT<OWN && PREC == PREC_SLAB>;
+
 // ------------------------------------------------------------------ kernel body
 // Trace one ray to completion with the layout's step function.
-template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ void trace_lane(const TraceArgs &a, Lane &L, Stack &st, Counts &cnt) {
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS, class S>
+__device__ __forceinline__ void step_any_layout(const TraceArgs &a, Lane &L, S &st, Counts &cnt) {
+  if constexpr (OWN && PREC == PREC_SLAB) step_slab<CREF, ANY, STATS>(a, L, st, cnt);
+  else if constexpr (OWN) step_bin<PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
+  else step_wide<W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
+}
+
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS, class S>
+__device__ __forceinline__ void trace_lane(const TraceArgs &a, Lane &L, S &st, Counts &cnt) {
   while (L.cur != kEmptyRef) {
     if (++L.steps > a.max_steps) {
       L.err = kErrIter;
       L.cur = kEmptyRef;
       break;
     }
-    if constexpr (OWN) step_bin<PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
-    else step_wide<W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
+    step_any_layout<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
   }
 }
 
 // Persistent warps: each warp takes 32 consecutive rays with one atomicAdd on
 // the global counter, every lane traces one of them to completion, repeat.
-template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ void body_warp_batch(const TraceArgs &a, Stack &st) {
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS, class S>
+__device__ __forceinline__ void body_warp_batch(const TraceArgs &a, S &st) {
   Counts cnt;
   uint32_t n_rays = 0;
   const uint32_t lane = threadIdx.x & 31u;
@@ -610,8 +737,7 @@ __device__ __forceinline__ void body_warp_batch(const TraceArgs &a, Stack &st) {
     L.err = 0;
     L.found = false;
     st.sp = 0;
-    if constexpr (OWN) L.cur = a.n_nodes > 0 ? 0u : kEmptyRef;
-    else L.cur = a.root_ref;
+    start_ray<OWN, PREC>(a, L);
     if (STATS) n_rays++;
     trace_lane<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
     if (L.err) atomicCAS(a.status, 0u, L.err);
@@ -649,8 +775,8 @@ __device__ __forceinline__ void body_warp_batch(const TraceArgs &a, Stack &st) {
 // warp are idle; then the warp takes that many consecutive rays of its CTA's
 // share with one shared-memory atomicAdd and the idle lanes set them up
 // together (refill_min = 1: a lane is refilled at the next step).
-template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ void body_refill(const TraceArgs &a, Stack &st) {
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS, class S>
+__device__ __forceinline__ void body_refill(const TraceArgs &a, S &st) {
   __shared__ uint32_t cta_next;
   if (threadIdx.x == 0) cta_next = 0;
   __syncthreads();
@@ -683,8 +809,7 @@ __device__ __forceinline__ void body_refill(const TraceArgs &a, Stack &st) {
           L.err = 0;
           L.found = false;
           st.sp = 0;
-          if constexpr (OWN) L.cur = a.n_nodes > 0 ? 0u : kEmptyRef;
-          else L.cur = a.root_ref;
+          start_ray<OWN, PREC>(a, L);
           has_ray = true;
           if (STATS) n_rays++;
         }
@@ -699,8 +824,7 @@ __device__ __forceinline__ void body_refill(const TraceArgs &a, Stack &st) {
         L.err = kErrIter;
         L.cur = kEmptyRef;
       } else {
-        if constexpr (OWN) step_bin<PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
-        else step_wide<W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
+        step_any_layout<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
       }
     }
     if (has_ray && L.cur == kEmptyRef) {
@@ -727,8 +851,10 @@ __device__ __forceinline__ void body_refill(const TraceArgs &a, Stack &st) {
 template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
 __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
   extern __shared__ uint2 smem_stack[];
-  Stack st;
+  StackFor<OWN, PREC> st;
   st.sh = smem_stack + threadIdx.x;
+  // exit distances (shared-slab layout) follow the entry columns
+  st.shf = reinterpret_cast<float *>(smem_stack + blockDim.x * a.smem_stack) + threadIdx.x;
   st.stride = blockDim.x;
   st.cap_sh = (int)a.smem_stack;
   st.sp = 0;

@@ -1,6 +1,6 @@
 // Instantiates the traversal kernels of one node family. Compiled several
-// times with -DSCION_OWN=1 -DSCION_PREC=<0|3|4> (own-box node with f32, q16
-// or eq10 boxes), or -DSCION_W=<2|4|8> -DSCION_PREC=<0|1|2|5>, so the families
+// times with -DSCION_OWN=1 -DSCION_PREC=<0|3|4|6> (own-box node with f32, q16
+// or eq10 boxes, or the shared-slab node), or -DSCION_W=<2|4|8> -DSCION_PREC=<0|1|2|5>, so the families
 // build in parallel.
 #include "cpq.cuh"
 #include "kernels.h"
@@ -39,16 +39,21 @@ TraceKernel SCION_GETTER(int soa, int cref, int any, int stats) {
   return table[soa & 1][cref & 1][any & 1][stats & 1];
 }
 
+
+#if SCION_FAMILY_OWN && SCION_PREC == 6
+// the shared-slab node carries ray intervals, not boxes: no closest point query
+TraceKernel SCION_CPQ_GETTER(int, int, int) { return nullptr; }
+#else
 template <int SOA, int CREF, bool STATS>
 __global__ void __launch_bounds__(kMaxThreadsPerBlock, kMinBlocksPerSm) cpq_kernel(TraceArgs a) {
   cpq_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, STATS>(a);
 }
-
 TraceKernel SCION_CPQ_GETTER(int soa, int cref, int stats) {
   static const TraceKernel table[2][2][2] = {
       {{cpq_kernel<0, 0, false>, cpq_kernel<0, 0, true>}, {cpq_kernel<0, 1, false>, cpq_kernel<0, 1, true>}},
       {{cpq_kernel<1, 0, false>, cpq_kernel<1, 0, true>}, {cpq_kernel<1, 1, false>, cpq_kernel<1, 1, true>}}};
   return table[soa & 1][cref & 1][stats & 1];
 }
+#endif
 
 }  // namespace scion

@@ -54,7 +54,7 @@ class DebugInfo(ctypes.Structure):
                 ("vert_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
 
 
-PREC = {"f32": 0, "f16": 1, "u8": 2, "q16": 3, "eq10": 4, "u16": 5}
+PREC = {"f32": 0, "f16": 1, "u8": 2, "q16": 3, "eq10": 4, "u16": 5, "slab": 6}
 ORDER = {"dfs": 0, "bfs": 1, "treelet": 2}
 
 
@@ -76,15 +76,17 @@ SWEEP = {
 }
 
 
-# Further layouts of Table 1: the world-grid quantised bvh2 layouts (Section
-# 9.2.5, App. D.1, D.3: sg-pbrt-q16, sg-pbrt-q16-soaos, sg-eq, sg-eq-align16)
-# and the 16-bit parent-relative 8-wide node (bvh8-q16).
+# Further layouts: the world-grid quantised bvh2 layouts of Table 1 (Section
+# 9.2.5, App. D.1, D.3: sg-pbrt-q16, sg-pbrt-q16-soaos, sg-eq, sg-eq-align16),
+# the 16-bit parent-relative 8-wide node (bvh8-q16) and the shared-slab bvh2
+# node with tree-carried bounds (Section 8.3).
 SWEEP_EXTENDED = {
     "bvh2_aos_q16": dict(width=2, box_layout="aos", box_prec="q16"),
     "bvh2_soa_q16": dict(width=2, box_layout="soa", box_prec="q16"),
     "bvh2_aos_eq10": dict(width=2, box_layout="aos", box_prec="eq10"),
     "bvh2_aos_eq10_a16": dict(width=2, box_layout="aos", box_prec="eq10", align=16),
     "bvh8_aos_u16": dict(width=8, box_layout="aos", box_prec="u16"),
+    "bvh2_slab": dict(width=2, box_layout="aos", box_prec="slab"),
 }
 
 

@@ -3,16 +3,17 @@ parity tests use the same list)."""
 import itertools
 
 WORLD_GRID = ("q16", "eq10")
+OWN_ONLY = WORLD_GRID + ("slab",)  # width-2 own-box-like nodes only
 
 
 def all_layouts():
     out = []
     for w, lay, prec, cref, pref, order in itertools.product(
-            (2, 4, 8), ("aos", "soa"), ("f32", "f16", "u8", "u16") + WORLD_GRID, ("direct", "indirect"),
+            (2, 4, 8), ("aos", "soa"), ("f32", "f16", "u8", "u16") + OWN_ONLY, ("direct", "indirect"),
             ("direct", "indirect"), ("dfs", "bfs", "treelet")):
-        if prec in WORLD_GRID and (w != 2 or (prec == "eq10" and lay == "soa")):
+        if prec in OWN_ONLY and (w != 2 or (prec in ("eq10", "slab") and lay == "soa")):
             continue
-        own = w == 2 and prec in ("f32",) + WORLD_GRID
+        own = w == 2 and prec in ("f32",) + OWN_ONLY
         if own and cref == "direct" and order != "dfs":
             continue
         out.append(dict(width=w, box_layout=lay, box_prec=prec, child_ref=cref, prim_ref=pref, order=order))

@@ -13,7 +13,7 @@ from paper_2511_15028_gb300 import scenes
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ALL = all_layouts()
+ALL = [kw for kw in all_layouts() if kw["box_prec"] != "slab"]  # slab: no CPQ
 
 
 @pytest.fixture(scope="module")
@@ -104,3 +104,7 @@ def test_soup_gpu_built_refit_and_counting(sc_mod, oracle_mod):
         same(query(sc_mod, bvh, pts), oracle_mod.cpq_brute(moved.reshape(-1, 9), pts), f"refit {kw}")
     with pytest.raises(sc_mod.ScionError):
         query(sc_mod, bvh, pts, dict(rays_per_fetch=1))
+    slab = sc_mod.scion_build(soup, sc_mod.layout(box_prec="slab"))
+    with pytest.raises(sc_mod.ScionError) as e:
+        query(sc_mod, slab, pts)
+    assert e.value.status == 2  # unsupported layout

@@ -9,7 +9,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
-from layout_cases import WORLD_GRID, all_layouts
+from layout_cases import OWN_ONLY, WORLD_GRID, all_layouts
 from paper_2511_15028_gb300 import scenes, scion
 
 
@@ -112,7 +112,8 @@ def test_pbrt_node_size_and_wide_sizes():
     for kw, per_node in ((dict(box_prec="q16"), 16), (dict(box_prec="q16", box_layout="soa"), 16),
                          (dict(box_prec="eq10"), 12), (dict(box_prec="eq10", align=16), 16),
                          (dict(box_prec="q16", box_layout="soa", align=16), 20),
-                         (dict(box_layout="soa", align=16), 40), (dict(align=16), 32)):
+                         (dict(box_layout="soa", align=16), 40), (dict(align=16), 32),
+                         (dict(box_prec="slab"), 16)):
         i = scion.scion_debug_build_host(sc.verts, scion.layout(**kw), sc.indices).info
         assert i["own_box"] == 1 and i["node_bytes"] == per_node * i["n_nodes"], kw
 
@@ -125,8 +126,8 @@ def test_soup_extreme_coordinates_enclosure():
         v = scenes.random_soup(rng, 3000, mu=math.log(0.01)) * scale + offset
         v = v.astype(np.float32)
         tris = v.reshape(-1, 9)
-        for prec in ("f32", "f16", "u8", "u16") + WORLD_GRID:
-            for w in ((2,) if prec in WORLD_GRID else (2, 4, 8)):
+        for prec in ("f32", "f16", "u8", "u16") + OWN_ONLY:
+            for w in ((2,) if prec in OWN_ONLY else (2, 4, 8)):
                 dec = scion.scion_debug_build_host(v, scion.layout(width=w, box_prec=prec))
                 sub, leaves = walk(dec)
                 check_enclosure(dec, sub, tris)
@@ -175,10 +176,11 @@ def test_nonfinite_triangles_left_out_and_empty_scene():
 
 def test_invalid_descriptors_rejected():
     v = scenes.config1_scene().triangles().reshape(-1, 3)
-    bad = [dict(width=3), dict(width=16), dict(box_prec=6), dict(order=3), dict(leaf_max=17),
+    bad = [dict(width=3), dict(width=16), dict(box_prec=7), dict(order=3), dict(leaf_max=17),
            dict(sah_bins=1), dict(sah_bins=65), dict(align=1), dict(align=32),
            dict(width=4, box_prec=3), dict(width=8, box_prec=4), dict(box_prec=3, leaf_max=16),
            dict(box_prec=4, box_layout=1), dict(width=2, box_prec=3, child_ref=0, order=1),
+           dict(width=4, box_prec=6), dict(box_prec=6, box_layout=1), dict(box_prec=6, child_ref=0, order=2),
            dict(width=2, box_prec=0, child_ref=0, order=1), dict(width=2, box_prec=0, child_ref=0, order=2)]
     for b in bad:
         d = scion.layout()
@@ -373,3 +375,34 @@ def test_world_grid_limits():
         _, leaves = walk(dec)
         assert sum(len(l) for l in leaves) == 10
         check_world_grid(dec)
+
+
+def test_shared_slab_carried_boxes_independent():
+    """Shared-slab layout (Section 8.3): decode the carried boxes top-down from
+    the raw node bytes (root = frame; a child takes its parent's box with one
+    plane replaced), compare with the library's decode, and check that every
+    carried box encloses its subtree's triangles and lies inside its parent's."""
+    sc = scenes.config2_scene(side=65, n_spheres=16)
+    tris = sc.triangles()
+    for kw in (dict(box_prec="slab"), dict(box_prec="slab", child_ref="indirect", order="bfs")):
+        dec = scion.scion_debug_build_host(sc.verts, scion.layout(**kw), sc.indices)
+        n = dec.info["n_nodes"]
+        raw = dec.nodes.reshape(n, 16)
+        planes = raw[:, :8].copy().view("<f4")
+        field = raw[:, 8:12].copy().view("<u4").ravel()
+        meta = raw[:, 12:16].copy().view("<u4").ravel()
+        box = np.full((n, 6), np.nan, np.float32)
+        box[0] = dec.frame[:6]
+        for x in range(n):  # parents precede children in every order
+            if meta[x] & 0xFFFF:
+                continue
+            ax = (meta[x] >> 16) & 3
+            l, r = (x + 1, x + field[x]) if kw.get("child_ref") != "indirect" else (field[x], field[x] + 1)
+            box[l] = box[x]
+            box[r] = box[x]
+            box[l, 3 + ax] = planes[x, 0]
+            box[r, ax] = planes[x, 1]
+            assert box[l, 3 + ax] <= box[x, 3 + ax] and box[r, ax] >= box[x, ax]
+        assert np.array_equal(box.view(np.uint32), dec.own_boxes.view(np.uint32))
+        sub, _ = walk(dec)
+        check_enclosure(dec, sub, tris)
