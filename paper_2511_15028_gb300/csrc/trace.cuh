@@ -320,6 +320,11 @@ struct WideNode {
   static constexpr int kBytes = kRefOff + (CREF == REF_DIRECT ? 4 * W : 8 + W);
   static constexpr int kStride = (kBytes + 31) & ~31;
   static constexpr int NQ = (kBytes + 15) / 16;
+  // SoA sub-word boxes whose coordinate rows are whole words: the near/far
+  // choice of an axis is made once per word for all children in it
+  static constexpr bool kRowSel = SOA && kElem < 4 && (W * kElem) % 4 == 0;
+  static constexpr int kRowWords = (W * kElem) / 4;
+  static constexpr int kPerWord = 4 / kElem;
 
   static __device__ __forceinline__ int box_off(int k, int c) {
     return kHdr + (SOA ? (c * W + k) : (k * 6 + c)) * kElem;
@@ -434,17 +439,63 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
       base_node = qword(q, N::kRefOff / 4);
       base_prim = qword(q, N::kRefOff / 4 + 1);
     }
+    // reference of child k (in increasing k: indirect leaves accumulate)
+    auto child_ref = [&](int k) -> uint32_t {
+      if (CREF == REF_DIRECT) return qword(q, N::kRefOff / 4 + k);
+      const uint32_t m = (qword(q, N::kRefOff / 4 + 2 + (k >> 2)) >> ((k & 3) * 8)) & 0xFFu;
+      if (m == 0) return kEmptyRef;
+      if (m & kMetaInterior) return ref_interior(base_node + (m & 0x7Fu));
+      const uint32_t rf = ref_leaf(base_prim + leaf_acc, m);
+      leaf_acc += m;
+      return rf;
+    };
+    if constexpr (N::kRowSel) {
+      constexpr int kRow = N::kRowWords;
+#pragma unroll
+      for (int j = 0; j < kRow; ++j) {
+        // word j of each coordinate row: near and far planes of its children
+        uint32_t nw[3], fw[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const uint32_t lw = qword(q, N::kHdr / 4 + c * kRow + j), hw = qword(q, N::kHdr / 4 + (c + 3) * kRow + j);
+          const bool neg = c == 0 ? r.nx : (c == 1 ? r.ny : r.nz);
+          nw[c] = neg ? hw : lw;
+          fw[c] = neg ? lw : hw;
+        }
+#pragma unroll
+        for (int i = 0; i < N::kPerWord; ++i) {
+          const int k = j * N::kPerWord + i;
+          const uint32_t ref = child_ref(k);
+          const uint32_t b = (uint32_t)(i * N::kElem);  // byte of the child in the word
+          float t0[3], t1[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float rc = c == 0 ? r.rx : (c == 1 ? r.ry : r.rz), oc = c == 0 ? r.orx : (c == 1 ? r.ory : r.orz);
+            if (N::kGrid) {
+              const uint32_t sel = N::kElem == 1 ? (0x7540u | b) : (0x7400u | ((b + 1u) << 4) | b);
+              const float nq = __uint_as_float(__byte_perm(nw[c], 0x4B000000u, sel)) - 8388608.0f;
+              const float fq = __uint_as_float(__byte_perm(fw[c], 0x4B000000u, sel)) - 8388608.0f;
+              const float ac = c == 0 ? ax : (c == 1 ? ay : az), bc = c == 0 ? bx : (c == 1 ? by : bz);
+              t0[c] = fmaf(nq, ac, bc);
+              t1[c] = fmaf(fq, ac, bc);
+            } else {
+              const float nv = __half2float(__ushort_as_half((unsigned short)((nw[c] >> (b * 8)) & 0xFFFFu)));
+              const float fv = __half2float(__ushort_as_half((unsigned short)((fw[c] >> (b * 8)) & 0xFFFFu)));
+              t0[c] = fmaf(nv, rc, -oc);
+              t1[c] = fmaf(fv, rc, -oc);
+            }
+          }
+          float tn;
+          bool hit = slab_t(r, t0[0], t0[1], t0[2], t1[0], t1[1], t1[2], tlim, tn);
+          hit = hit && ref != kEmptyRef;
+          cref[k] = hit ? ref : kEmptyRef;
+          ctn[k] = hit ? tn : __int_as_float(0x7f800000);
+        }
+      }
+    } else {
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      uint32_t ref;
-      if (CREF == REF_DIRECT) {
-        ref = qword(q, N::kRefOff / 4 + k);
-      } else {
-        const uint32_t m = (qword(q, N::kRefOff / 4 + 2 + (k >> 2)) >> ((k & 3) * 8)) & 0xFFu;
-        if (m == 0) ref = kEmptyRef;
-        else if (m & kMetaInterior) ref = ref_interior(base_node + (m & 0x7Fu));
-        else { ref = ref_leaf(base_prim + leaf_acc, m); leaf_acc += m; }
-      }
+      const uint32_t ref = child_ref(k);
       float tn;
       bool hit;
       if (N::kGrid) {
@@ -473,6 +524,7 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
       hit = hit && ref != kEmptyRef;
       cref[k] = hit ? ref : kEmptyRef;
       ctn[k] = hit ? tn : __int_as_float(0x7f800000);
+    }
     }
     if (!ANY && a.ordered == 1) {
       sort_children<W>(ctn, cref);

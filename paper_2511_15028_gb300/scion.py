@@ -86,6 +86,7 @@ SWEEP_EXTENDED = {
     "bvh2_aos_eq10": dict(width=2, box_layout="aos", box_prec="eq10"),
     "bvh2_aos_eq10_a16": dict(width=2, box_layout="aos", box_prec="eq10", align=16),
     "bvh8_aos_u16": dict(width=8, box_layout="aos", box_prec="u16"),
+    "bvh8_soa_u8": dict(width=8, box_layout="soa", box_prec="u8"),
     "bvh2_slab": dict(width=2, box_layout="aos", box_prec="slab"),
 }
 
