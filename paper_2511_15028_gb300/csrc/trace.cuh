@@ -537,12 +537,25 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
     // push every hit child but the first, last one first; go on with the first
     uint32_t next = kEmptyRef;
     float next_tn = 0.f;
+    if (st.sp + W <= st.cap_sh) {
+      // room in shared memory for any node: predicated stores, one check
+      int sp = st.sp;
 #pragma unroll
-    for (int k = W - 1; k >= 0; --k) {
-      if (cref[k] == kEmptyRef) continue;
-      if (next != kEmptyRef && !st.push(next, next_tn)) { L.err = kErrStack; L.cur = kEmptyRef; return; }
-      next = cref[k];
-      next_tn = ctn[k];
+      for (int k = W - 1; k >= 0; --k) {
+        const bool h = cref[k] != kEmptyRef;
+        if (h && next != kEmptyRef) st.sh[(sp++) * st.stride] = make_uint2(next, __float_as_uint(next_tn));
+        next = h ? cref[k] : next;
+        next_tn = h ? ctn[k] : next_tn;
+      }
+      st.sp = sp;
+    } else {
+#pragma unroll
+      for (int k = W - 1; k >= 0; --k) {
+        if (cref[k] == kEmptyRef) continue;
+        if (next != kEmptyRef && !st.push(next, next_tn)) { L.err = kErrStack; L.cur = kEmptyRef; return; }
+        next = cref[k];
+        next_tn = ctn[k];
+      }
     }
     L.cur = next != kEmptyRef ? next : pop_next<ANY>(st, L.b.t);
   } else {
