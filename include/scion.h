@@ -195,9 +195,10 @@ scion_status scion_build_many(const float *verts, uint64_t n_verts, const uint32
  * (Section 5.1 keeps construction apart from the layout build; Section 2:
  * topology is orthogonal to layout) as a linear BVH: 30-bit Morton codes of
  * the triangle centroids, a stable radix sort, the binary radix tree of
- * Karras (2012) and boxes bottom-up; one triangle per leaf (leaf_max and
- * sah_bins are not used). The tree is then packed into `desc` by the same
- * host packers as scion_build.
+ * Karras (2012) and boxes bottom-up; a subtree of at most leaf_max triangles
+ * becomes one leaf where the surface area heuristic prefers it to splitting
+ * (sah_bins is not used). The tree is then packed
+ * into `desc` by the same host packers as scion_build.
  *  d_verts   : float [n_verts][3], DEVICE memory (read, not retained).
  *  d_indices : uint32 [n_tris][3] in DEVICE memory, or NULL for a soup.
  *  stream    : stream for the build kernels and copies; the call returns

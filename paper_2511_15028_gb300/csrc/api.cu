@@ -508,7 +508,7 @@ scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint3
     LogicalBVH lb;
     double gpu_ms = 0.0;
     std::string err;
-    st = lbvh_build(d_verts, n_verts, d_indices, n_tris, s, &lb, &gpu_ms, &err);
+    st = lbvh_build(d_verts, n_verts, d_indices, n_tris, d.leaf_max, s, &lb, &gpu_ms, &err);
     if (st != SCION_OK) {
       g_last_error = err;
       return st;

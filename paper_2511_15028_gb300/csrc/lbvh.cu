@@ -257,7 +257,7 @@ __device__ __forceinline__ int delta(const uint32_t *keys, int n, int i, int j) 
 }
 
 __global__ void radix_tree_kernel(const uint32_t *__restrict__ keys, int n, uint32_t *left, uint32_t *right,
-                                  uint32_t *parent, uint8_t *axis) {
+                                  uint32_t *parent, uint8_t *axis, uint32_t *range_lo, uint32_t *range_hi) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += gridDim.x * blockDim.x) {
     const int d = delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1) >= 0 ? 1 : -1;
     const int dmin = delta(keys, n, i, i - d);
@@ -282,6 +282,8 @@ __global__ void radix_tree_kernel(const uint32_t *__restrict__ keys, int n, uint
     const uint32_t rc = hi == g + 1 ? (uint32_t)(n - 1 + g + 1) : (uint32_t)(g + 1);
     left[i] = lc;
     right[i] = rc;
+    range_lo[i] = (uint32_t)lo;  // the node's leaves: sorted triangles lo..hi
+    range_hi[i] = (uint32_t)hi;
     parent[lc] = (uint32_t)i;
     parent[rc] = (uint32_t)i;
     // split axis: the highest bit in which the range's end codes differ
@@ -349,7 +351,7 @@ int grid_for(uint64_t n, int threads) {
 }  // namespace
 
 scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices, uint64_t n_tris,
-                        cudaStream_t s, LogicalBVH *out, double *gpu_ms, std::string *err) {
+                        uint32_t leaf_max, cudaStream_t s, LogicalBVH *out, double *gpu_ms, std::string *err) {
   (void)n_verts;
   out->nodes.clear();
   out->prims.clear();
@@ -414,11 +416,13 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
     return SCION_OK;
   }
   const size_t nn = 2 * (size_t)nv - 1;
-  uint32_t *left, *right, *parent, *arrived;
+  uint32_t *left, *right, *parent, *arrived, *rlo, *rhi;
   uint8_t *axis;
   float *nlo, *nhi;
   SCION_LB(sc.get(&left, nv));
   SCION_LB(sc.get(&right, nv));
+  SCION_LB(sc.get(&rlo, nv));
+  SCION_LB(sc.get(&rhi, nv));
   SCION_LB(sc.get(&axis, nv));
   SCION_LB(sc.get(&parent, nn));
   SCION_LB(sc.get(&arrived, nv));
@@ -427,7 +431,8 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
   SCION_LB(cudaMemsetAsync(parent, 0xFF, nn * sizeof(uint32_t), s));
   SCION_LB(cudaMemsetAsync(arrived, 0, nv * sizeof(uint32_t), s));
   if (nv > 1) {
-    radix_tree_kernel<<<grid_for(nv - 1, 256), 256, 0, s>>>(keys[cur], (int)nv, left, right, parent, axis);
+    radix_tree_kernel<<<grid_for(nv - 1, 256), 256, 0, s>>>(keys[cur], (int)nv, left, right, parent, axis, rlo,
+                                                             rhi);
     SCION_LB(cudaGetLastError());
   }
   boxes_kernel<<<grid_for(nv, 256), 256, 0, s>>>((int)nv, vals[cur], tlo, thi, left, right, parent, nlo, nhi,
@@ -435,13 +440,15 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
   SCION_LB(cudaGetLastError());
   SCION_LB(cudaEventRecord(ev1, s));
   // download the tree
-  std::vector<uint32_t> hl(nv), hr(nv), ids(nv);
+  std::vector<uint32_t> hl(nv), hr(nv), ids(nv), hrl(nv), hrh(nv);
   std::vector<uint8_t> hax(nv);
   std::vector<float> hlo(3 * nn), hhi(3 * nn);
   SCION_LB(cudaMemcpyAsync(ids.data(), vals[cur], nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   SCION_LB(cudaMemcpyAsync(hl.data(), left, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   SCION_LB(cudaMemcpyAsync(hr.data(), right, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   SCION_LB(cudaMemcpyAsync(hax.data(), axis, nv, cudaMemcpyDeviceToHost, s));
+  SCION_LB(cudaMemcpyAsync(hrl.data(), rlo, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  SCION_LB(cudaMemcpyAsync(hrh.data(), rhi, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   SCION_LB(cudaMemcpyAsync(hlo.data(), nlo, 3 * nn * sizeof(float), cudaMemcpyDeviceToHost, s));
   SCION_LB(cudaMemcpyAsync(hhi.data(), nhi, 3 * nn * sizeof(float), cudaMemcpyDeviceToHost, s));
   SCION_LB(cudaStreamSynchronize(s));
@@ -449,26 +456,82 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
   SCION_LB(cudaEventElapsedTime(&ms, ev0, ev1));
   *gpu_ms = ms;
 #undef SCION_LB
+  // Leaves. A subtree covers a contiguous range of the sorted triangles, so
+  // it can become one leaf over that range. Bottom-up, each subtree of at
+  // most leaf_max triangles is kept whole when that is cheaper under the
+  // surface area heuristic than its best split (node and triangle test cost
+  // 1 each, as in the host builder): cost = min(area * count, area +
+  // cost(left) + cost(right)).
+  const uint32_t lmax = leaf_max ? leaf_max : 1u;
+  auto area_of = [&](uint32_t x) {
+    const double ex = (double)hhi[3 * (size_t)x] - hlo[3 * (size_t)x];
+    const double ey = (double)hhi[3 * (size_t)x + 1] - hlo[3 * (size_t)x + 1];
+    const double ez = (double)hhi[3 * (size_t)x + 2] - hlo[3 * (size_t)x + 2];
+    return 2.0 * (ex * ey + ey * ez + ez * ex);
+  };
+  std::vector<uint8_t> whole(nv > 1 ? nv - 1 : 0, 0);
+  if (nv > 1 && lmax > 1) {
+    std::vector<double> cost(nv - 1);
+    std::vector<uint32_t> pre, todo_c{0u};
+    pre.reserve(nv - 1);
+    while (!todo_c.empty()) {  // pre-order of the interior nodes
+      const uint32_t x = todo_c.back();
+      todo_c.pop_back();
+      pre.push_back(x);
+      if (hl[x] + 1 < nv) todo_c.push_back(hl[x]);
+      if (hr[x] + 1 < nv) todo_c.push_back(hr[x]);
+    }
+    auto cost_of = [&](uint32_t x) { return x + 1 < nv ? cost[x] : area_of(x); };
+    for (size_t i = pre.size(); i-- > 0;) {  // children before parents
+      const uint32_t x = pre[i];
+      const double a = area_of(x);
+      const double split = a + cost_of(hl[x]) + cost_of(hr[x]);
+      const uint32_t n = hrh[x] - hrl[x] + 1;
+      const double leaf = n <= lmax ? a * (double)n : INFINITY;
+      whole[x] = leaf <= split ? 1 : 0;
+      cost[x] = whole[x] ? leaf : split;
+    }
+  }
+  // Logical tree, depth first from the root.
   out->prims = std::move(ids);
-  out->nodes.resize(nn);
-  for (size_t x = 0; x < nn; ++x) {
-    LNode &d = out->nodes[x];
+  out->nodes.reserve(nn);
+  struct Item {
+    uint32_t src, dst;  // node of the radix tree, node of the logical tree
+  };
+  std::vector<Item> todo;
+  auto box_of = [&](uint32_t x) {
+    Box3 b;
     for (int a = 0; a < 3; ++a) {
-      d.box.lo[a] = hlo[3 * x + a];
-      d.box.hi[a] = hhi[3 * x + a];
+      b.lo[a] = hlo[3 * (size_t)x + a];
+      b.hi[a] = hhi[3 * (size_t)x + a];
     }
-    if (x + 1 < nv) {  // interior
-      d.left = hl[x];
-      d.right = hr[x];
-      d.first = 0;
-      d.count = 0;
-      d.axis = hax[x];
-    } else {  // leaf k = x - (nv - 1)
-      d.left = d.right = 0;
-      d.first = (uint32_t)(x - (nv - 1));
+    return b;
+  };
+  auto emit = [&](uint32_t src) {
+    LNode d{};
+    d.box = box_of(src);
+    const uint32_t id = (uint32_t)out->nodes.size();
+    if (src + 1 >= nv) {  // a leaf of the radix tree: one triangle
+      d.first = src - (nv - 1);
       d.count = 1;
-      d.axis = 0;
+    } else if (whole[src]) {
+      d.first = hrl[src];
+      d.count = hrh[src] - hrl[src] + 1;
+    } else {
+      d.axis = hax[src];
+      todo.push_back(Item{src, id});
     }
+    out->nodes.push_back(d);
+    return id;
+  };
+  emit(0);
+  while (!todo.empty()) {
+    const Item it = todo.back();
+    todo.pop_back();
+    const uint32_t l = emit(hl[it.src]);
+    const uint32_t r = emit(hr[it.src]);
+    out->nodes[it.dst].left = l;
+    out->nodes[it.dst].right = r;
   }
   return SCION_OK;
 }

@@ -5,8 +5,10 @@
 // Linear BVH: triangles are ordered along a 30-bit Morton curve of their box
 // centres (Lauterbach et al. 2009), the binary radix tree over the sorted
 // codes is built with one thread per interior node (Karras 2012), and boxes
-// are computed bottom-up. One triangle per leaf. The result is the same
-// LogicalBVH the host SAH builder produces, so every packer and layout
+// are computed bottom-up. A subtree of at most leaf_max triangles (a
+// contiguous range of the sorted order) becomes one leaf where the surface
+// area heuristic prefers it to the subtree's best split. The result is the
+// same LogicalBVH the host SAH builder produces, so every packer and layout
 // applies unchanged.
 #pragma once
 
@@ -22,6 +24,6 @@ namespace scion {
 // `stream` before returning. *gpu_ms receives the device time of the build
 // kernels (bounds, codes, sort, tree, boxes), without the download.
 scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices, uint64_t n_tris,
-                        cudaStream_t stream, LogicalBVH *out, double *gpu_ms, std::string *err);
+                        uint32_t leaf_max, cudaStream_t stream, LogicalBVH *out, double *gpu_ms, std::string *err);
 
 }  // namespace scion

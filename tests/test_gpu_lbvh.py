@@ -65,7 +65,18 @@ def test_config1_gpu_built_every_family(sc_mod, oracle_mod, kw):
     t = sc_mod.scion_bvh_build_times(bvh)
     assert t["logical_ms"] > 0 and t["pack_ms"] >= 0
     if not kw:
-        assert bvh.info()["n_nodes"] == 2 * 4096 - 1  # one triangle per leaf, every triangle once
+        # leaf_max 1: one triangle per leaf, every triangle once; the default
+        # (4) collapses subtrees of up to 4 triangles into one leaf
+        one = sc_mod.scion_build_gpu(torch.from_numpy(sc.verts).cuda(), sc_mod.layout(leaf_max=1),
+                                     torch.from_numpy(sc.indices.astype(np.int32)).cuda())
+        assert one.info()["n_nodes"] == 2 * 4096 - 1
+        same(hits(sc_mod, one, rays), exp, "leaf_max=1")
+        assert bvh.info()["n_nodes"] < 2 * 4096 - 1
+        for lm in (2, 8, 15):
+            b = sc_mod.scion_build_gpu(torch.from_numpy(sc.verts).cuda(), sc_mod.layout(width=4, leaf_max=lm),
+                                       torch.from_numpy(sc.indices.astype(np.int32)).cuda())
+            same(hits(sc_mod, b, rays), exp, f"leaf_max={lm}")
+            assert np.array_equal(occluded(sc_mod, b, rays), occ)
 
 
 def test_soup_against_oracle_bvh_and_host_build(sc_mod, oracle_mod):
