@@ -212,9 +212,12 @@ def pick_fetch(scion, torch, bvh, fn, rays, out, reps=3):
 
 
 def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler=None):
-    """K timed steps of (primary closest, bounce closest, shadow any); events
-    on the launching stream around each launch. Each kind of ray uses the
-    fetch mode measured fastest for it."""
+    """K timed steps of primary closest hit, then bounce closest hit and
+    shadow any hit (both made from the primary hits, so they wait for it and
+    run concurrently on two streams). Events on each launch's own stream
+    around each launch; the step is timed on the main stream from before the
+    primary launch to after both others have joined. Each kind of ray uses
+    the fetch mode measured fastest for it."""
     d_p, d_b, d_s = rays
     o_p, o_b, o_s = outs
     fns = (scion.scion_trace_closest, scion.scion_trace_closest, scion.scion_trace_any)
@@ -222,28 +225,44 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
     modes = [m for m, _ in picks]
     ps = [FETCH_MODES[m] or None for m in modes]
     stream = torch.cuda.current_stream()
-    for _ in range(warmup):
+    s_b, s_s = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def one_step(e=None):
+        if e:
+            e[0].record(stream)
         scion.scion_trace_closest(bvh, d_p, o_p, params=ps[0])
-        scion.scion_trace_closest(bvh, d_b, o_b, params=ps[1])
-        scion.scion_trace_any(bvh, d_s, o_s, params=ps[2])
+        if e:
+            e[1].record(stream)
+        s_b.wait_stream(stream)
+        s_s.wait_stream(stream)
+        if e:
+            e[2].record(s_b)
+        scion.scion_trace_closest(bvh, d_b, o_b, params=ps[1], stream=s_b)
+        if e:
+            e[3].record(s_b)
+            e[4].record(s_s)
+        scion.scion_trace_any(bvh, d_s, o_s, params=ps[2], stream=s_s)
+        if e:
+            e[5].record(s_s)
+        stream.wait_stream(s_b)
+        stream.wait_stream(s_s)
+        if e:
+            e[6].record(stream)
+
+    for _ in range(warmup):
+        one_step()
     torch.cuda.synchronize()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
     t_start = time.time()
     for k in range(steps):
         flush_l2(flush_buf)
-        e = ev[k]
-        e[0].record(stream)
-        scion.scion_trace_closest(bvh, d_p, o_p, params=ps[0])
-        e[1].record(stream)
-        scion.scion_trace_closest(bvh, d_b, o_b, params=ps[1])
-        e[2].record(stream)
-        scion.scion_trace_any(bvh, d_s, o_s, params=ps[2])
-        e[3].record(stream)
+        one_step(ev[k])
     torch.cuda.synchronize()
     if sampler:
         sampler.window(t_start, time.time())
-    per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in ev])  # ms
-    step = per.sum(axis=1)
+    per = np.array([[e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3]), e[4].elapsed_time(e[5])]
+                    for e in ev])  # ms per launch
+    step = np.array([e[0].elapsed_time(e[6]) for e in ev])
     return step, per, modes, [t for _, t in picks]
 
 
@@ -251,7 +270,7 @@ def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("w
     """The same step through the public API from pinned host memory: every
     step copies its rays host->device and its results device->host, pipelined
     in chunks on three streams (scion.HostTracer) so that the copies overlap
-    the traversal."""
+    the traversal; bounce and shadow traces start after the primary traces."""
     h_in = [torch.from_numpy(r).pin_memory() for r in host_rays]
     n = [r.shape[0] for r in host_rays]
     h_out = [torch.empty((n[0], 4), dtype=torch.int32).pin_memory(),
@@ -262,15 +281,16 @@ def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("w
             (bvh, h_in[2], h_out[2], "any", ps[2])]
     tracer = scion.HostTracer()
     stream = torch.cuda.current_stream()
+    phases = [[0], [1, 2]]  # bounce and shadow rays come from the primary hits
     for _ in range(warmup):
-        tracer.trace(jobs)
+        tracer.trace(jobs, phases)
     torch.cuda.synchronize()
     times = []
     for _ in range(steps):
         flush_l2(flush_buf)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        tracer.trace(jobs)
+        tracer.trace(jobs, phases)
         b.record(stream)
         b.synchronize()
         times.append(a.elapsed_time(b))
@@ -367,7 +387,7 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
     short = rays.clone()
     short[:, 7] = 0.05
     gen_s = time.time() - t0
-    lays = scion.sweep_layouts(extended=True)
+    lays = scion.sweep_layouts(extended=True, orders=True)
     if only:
         lays = {k: v for k, v in lays.items() if k in only}
     t0 = time.time()
@@ -816,7 +836,9 @@ def main():
                 "kernel": f"trace_kernel closest hit ({best}; primary + bounce launches)",
                 "peak_source": peak_src,
                 "note": "algorithmic bytes = rays x 48 + nodes visited x node bytes + triangles tested x "
-                        "triangle bytes (counting kernel); this BVH fits in L2, so DRAM traffic is far lower"}
+                        "triangle bytes (counting kernel); this BVH fits in L2, so DRAM traffic is far lower; "
+                        "the bounce launch shares the GPU with the concurrent shadow launch, so its duration "
+                        "and this figure are conservative"}
     # end to end through host buffers, best layout
     fm = r["fetch_mode"]
     e2e_t, bi, bo = e2e_layout(scion, torch, r["_bvh"], (prim, bounce, shadow), args.steps, args.warmup, flush_buf,
@@ -851,7 +873,9 @@ def main():
             "config": {"workload": WORKLOAD, "layout": best, "rays_per_step": int(sum(n_rays)),
                        "rays": {"primary": n_rays[0], "bounce": n_rays[1], "shadow": n_rays[2]},
                        "l2": "flushed (512 MiB write) between timed steps",
-                       "timing": "CUDA events per launch; trimmed mean of K steps (drop 2/9 each side)",
+                       "timing": "primary closest hit, then bounce closest hit and shadow any hit concurrently "
+                                 "on two streams (both come from the primary hits); CUDA events per launch on its "
+                                 "stream and around the step on the main stream; trimmed mean of K steps",
                        "parallelism": f"replicas x{world}"},
             "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * args.steps,

@@ -17,6 +17,8 @@ from . import scion
 CANDIDATE_LAYOUTS = {
     "bvh2_aos_f32": dict(width=2, box_layout="aos", box_prec="f32"),
     "bvh4_soa_f32": dict(width=4, box_layout="soa", box_prec="f32"),
+    # breadth-first order: much faster once the BVH is far larger than L2
+    "bvh4_soa_f32_bfs": dict(width=4, box_layout="soa", box_prec="f32", order="bfs"),
     "bvh8_soa_f16": dict(width=8, box_layout="soa", box_prec="f16"),
     "bvh8_aos_u8": dict(width=8, box_layout="aos", box_prec="u8"),
 }

@@ -91,11 +91,24 @@ SWEEP_EXTENDED = {
 }
 
 
-def sweep_layouts(extended: bool = False):
+# Breadth-first node order for the wide layouts (the order axis: the levels
+# every ray visits sit together at the front of the node buffer instead of
+# being spread through it by depth-first subtrees).
+SWEEP_ORDER = {
+    "bvh4_soa_f32_bfs": dict(width=4, box_layout="soa", box_prec="f32", order="bfs"),
+    "bvh8_soa_f16_bfs": dict(width=8, box_layout="soa", box_prec="f16", order="bfs"),
+    "bvh8_aos_u8_bfs": dict(width=8, box_layout="aos", box_prec="u8", order="bfs"),
+}
+
+
+def sweep_layouts(extended: bool = False, orders: bool = False):
     """Named descriptors of the swept layouts, each with direct and indirect
-    triangle storage (plus the further Table 1 layouts if asked)."""
+    triangle storage (plus the further Table 1 layouts and the breadth-first
+    orders if asked)."""
     out = {}
-    sweep = dict(SWEEP, **SWEEP_EXTENDED) if extended else SWEEP
+    sweep = dict(SWEEP, **SWEEP_EXTENDED) if extended else dict(SWEEP)
+    if orders:
+        sweep.update(SWEEP_ORDER)
     for name, kw in sweep.items():
         for pr in ("direct", "indirect"):
             out[f"{name}_{pr}"] = layout(prim_ref=pr, **kw)
@@ -489,9 +502,10 @@ class HostTracer:
     chunk overlap the traversal of the others. Device staging buffers are
     allocated once (on first use) and reused."""
 
-    def __init__(self, n_streams: int = 3, chunk_rays: int = 1 << 19):
+    def __init__(self, n_streams: int = 3, chunk_rays: int = 1 << 20):
         import torch
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.join = torch.cuda.Stream()
         self.chunk = chunk_rays
         self._rays = [None] * n_streams
         self._outs = [None] * n_streams
@@ -506,34 +520,55 @@ class HostTracer:
             cache[i] = b
         return b[:n_rows]
 
-    def trace(self, jobs):
+    def trace(self, jobs, phases=None):
         """jobs: list of (bvh, host_rays [n, 8] float32 pinned, host_out
         pinned (int32 [n, 4] for closest, int32 [n] for any), query
-        ('closest' | 'any'), params or None). Issues everything and makes the
-        current stream wait for it: the host outputs are complete once the
-        current stream reaches this point (e.g. after an event on it)."""
+        ('closest' | 'any'), params or None). phases: optional list of lists
+        of job indices; the traces of a phase start only after every trace of
+        the previous phase has finished (e.g. [[0], [1, 2]]: bounce and shadow
+        rays that come from the primary hits), while copies are not held
+        back. Default: one phase with every job. Issues everything and makes
+        the current stream wait for it: the host outputs are complete once
+        the current stream reaches this point (e.g. after an event on it)."""
         import torch
         cur = torch.cuda.current_stream()
         for s in self.streams:
             s.wait_stream(cur)
+        if phases is None:
+            phases = [list(range(len(jobs)))]
         k = 0
-        for bvh, h_rays, h_out, query, params in jobs:
-            n = h_rays.shape[0]
-            for b in range(0, n, self.chunk):
-                e = min(n, b + self.chunk)
-                i = k % len(self.streams)
-                s = self.streams[i]
-                with torch.cuda.stream(s):
-                    d_r = self._buf(i, e - b, (8,), torch.float32, "rays")
-                    d_r.copy_(h_rays[b:e], non_blocking=True)
-                    if query == "closest":
-                        d_o = self._buf(i, e - b, (4,), torch.int32, "outs")
-                        scion_trace_closest(bvh, d_r, d_o, params=params, stream=s)
-                    else:
-                        d_o = self._any_buf(i, e - b)
-                        scion_trace_any(bvh, d_r, d_o, params=params, stream=s)
-                    h_out[b:e].copy_(d_o, non_blocking=True)
-                k += 1
+        prev_done = None
+        for pi, ph in enumerate(phases):
+            traced = []
+            for j in ph:
+                bvh, h_rays, h_out, query, params = jobs[j]
+                n = h_rays.shape[0]
+                for b in range(0, n, self.chunk):
+                    e = min(n, b + self.chunk)
+                    i = k % len(self.streams)
+                    s = self.streams[i]
+                    with torch.cuda.stream(s):
+                        d_r = self._buf(i, e - b, (8,), torch.float32, "rays")
+                        d_r.copy_(h_rays[b:e], non_blocking=True)
+                        if prev_done is not None:
+                            s.wait_event(prev_done)
+                        if query == "closest":
+                            d_o = self._buf(i, e - b, (4,), torch.int32, "outs")
+                            scion_trace_closest(bvh, d_r, d_o, params=params, stream=s)
+                        else:
+                            d_o = self._any_buf(i, e - b)
+                            scion_trace_any(bvh, d_r, d_o, params=params, stream=s)
+                        if pi + 1 < len(phases):
+                            ev = torch.cuda.Event()
+                            ev.record(s)
+                            traced.append(ev)
+                        h_out[b:e].copy_(d_o, non_blocking=True)
+                    k += 1
+            if traced:
+                for ev in traced:
+                    self.join.wait_event(ev)
+                prev_done = torch.cuda.Event()
+                prev_done.record(self.join)
         for s in self.streams:
             cur.wait_stream(s)
 

@@ -68,7 +68,7 @@ def test_config3_full_size(sc_mod, oracle_mod):
     eocc = oracle_mod.any_brute(tris, short[pick])
     assert 0.3 < (exp["prim"] != 0xFFFFFFFF).mean() and 0.02 < eocc.mean() < 0.98
     d, ds = torch.from_numpy(rays).cuda(), torch.from_numpy(short).cuda()
-    for name, desc in scion.sweep_layouts(extended=True).items():
+    for name, desc in scion.sweep_layouts(extended=True, orders=True).items():
         bvh = scion.scion_build(sc.verts, desc)
         got = scion.scion_trace_closest(bvh, d)[torch.from_numpy(pick).cuda()]
         _cmp(scion, got, exp, name + " closest")

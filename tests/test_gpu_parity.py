@@ -262,12 +262,17 @@ def test_concurrent_streams_same_bvh_and_host_tracer(sc_mod, oracle_mod):
     h_s = torch.from_numpy(short).pin_memory()
     h_o = torch.empty((rays.shape[0], 4), dtype=torch.int32).pin_memory()
     h_a = torch.empty((rays.shape[0],), dtype=torch.int32).pin_memory()
+    h_o2 = torch.empty((rays.shape[0], 4), dtype=torch.int32).pin_memory()
     tracer = sc_mod.HostTracer(n_streams=3, chunk_rays=30_000)
-    for p in (None, dict(rays_per_fetch=1)):
+    for p, phases in ((None, None), (dict(rays_per_fetch=1), None), (None, [[0], [1, 2]]),
+                      (dict(rays_per_fetch=8), [[2], [0], [1]])):
         h_o.fill_(0)
+        h_o2.fill_(0)
         h_a.fill_(7)
-        tracer.trace([(bvh, h_r, h_o, "closest", p), (bvh, h_s, h_a, "any", p)])
+        tracer.trace([(bvh, h_r, h_o, "closest", p), (bvh, h_s, h_a, "any", p), (bvh, h_r, h_o2, "closest", p)],
+                     phases)
         torch.cuda.synchronize()
-        assert_same_hits(sc_mod.split_hits(h_o), exp, f"host tracer {p}")
+        assert_same_hits(sc_mod.split_hits(h_o), exp, f"host tracer {p} {phases}")
+        assert_same_hits(sc_mod.split_hits(h_o2), exp, f"host tracer {p} {phases}")
         assert np.array_equal(h_a.numpy().astype(np.uint32), eocc)
     assert sc_mod.scion_get_status(bvh) == 0
