@@ -192,8 +192,7 @@ __device__ __forceinline__ void cp_step_wide(const TraceArgs &a, CpLane &L, Stac
   if (STATS) cnt.nodes++;
   const uint4 *np = a.nodes + (size_t)ref_node(cur) * (N::kStride / 16);
   uint4 q[N::NQ];
-#pragma unroll
-  for (int i = 0; i < N::NQ; ++i) q[i] = ldg4(np + i);
+  load_node<N::NQ>(np, q);
   float ox = 0.f, oy = 0.f, oz = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
   if (N::kGrid) {
     ox = __uint_as_float(q[0].x); oy = __uint_as_float(q[0].y); oz = __uint_as_float(q[0].z);
@@ -272,7 +271,8 @@ __device__ __forceinline__ void own_node(const TraceArgs &a, uint32_t x, float (
       hi[0] = __uint_as_float(b1.y); hi[1] = __uint_as_float(b2.x); hi[2] = __uint_as_float(b2.y);
       ref = rm.x; meta = rm.y;
     } else {
-      const uint4 q0 = ldg4(a.nodes + 2 * (size_t)x), q1 = ldg4(a.nodes + 2 * (size_t)x + 1);
+      uint4 q0, q1;
+      ldg8(a.nodes + 2 * (size_t)x, q0, q1);
       lo[0] = __uint_as_float(q0.x); lo[1] = __uint_as_float(q0.y); lo[2] = __uint_as_float(q0.z);
       hi[0] = __uint_as_float(q0.w); hi[1] = __uint_as_float(q1.x); hi[2] = __uint_as_float(q1.y);
       ref = q1.z; meta = q1.w;

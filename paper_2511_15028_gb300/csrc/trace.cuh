@@ -6,7 +6,7 @@
 // children-in-parent wide node of width W with f32/f16/u8 boxes, AoS or SoA,
 // direct or indirect child references) is a set of template parameters, so
 // every field access compiles to fixed offsets into registers loaded with
-// 128-bit non-coherent loads.
+// 256-bit non-coherent loads (node strides are multiples of 32 bytes).
 //
 // Execution model: a persistent grid (a few CTAs per SM); each warp takes 32
 // rays at a time from a global counter with one atomicAdd; each lane traces
@@ -207,6 +207,22 @@ __device__ __forceinline__ bool tri_test(const Ray &r, float4 p0, float4 p1, flo
 
 // ------------------------------------------------------------------ loads
 __device__ __forceinline__ uint4 ldg4(const uint4 *p) { return __ldg(p); }
+// 256-bit non-coherent load of two consecutive uint4 (p 32-byte aligned):
+// one L1 request per 32-byte sector instead of one per 16 bytes
+__device__ __forceinline__ void ldg8(const uint4 *p, uint4 &lo, uint4 &hi) {
+  asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+      : "l"(p));
+}
+// A node of NQ 16-byte words at a 32-byte aligned address (node strides are
+// multiples of 32 bytes and node buffers are separately allocated): 256-bit
+// loads, and a 128-bit load for an odd last word.
+template <int NQ>
+__device__ __forceinline__ void load_node(const uint4 *np, uint4 (&q)[NQ]) {
+#pragma unroll
+  for (int i = 0; i + 1 < NQ; i += 2) ldg8(np + i, q[i], q[i + 1]);
+  if constexpr ((NQ & 1) != 0) q[NQ - 1] = ldg4(np + NQ - 1);
+}
 __device__ __forceinline__ float4 ldg4f(const float4 *p) { return __ldg(p); }
 
 template <int NQ>
@@ -418,8 +434,7 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
     if (STATS) cnt.nodes++;
     const uint4 *np = a.nodes + (size_t)ref_node(cur) * (N::kStride / 16);
     uint4 q[N::NQ];
-#pragma unroll
-    for (int i = 0; i < N::NQ; ++i) q[i] = ldg4(np + i);
+    load_node<N::NQ>(np, q);
     // u8 / u16 frame: coordinate = origin + code * 2^e, folded into the plane
     // distance t = fma(code, 2^e / d, (origin - o) / d) per axis
     float ax = 0.f, bx = 0.f, ay = 0.f, by = 0.f, az = 0.f, bz = 0.f;
@@ -604,7 +619,8 @@ __device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, Stack &st,
       hi0 = __uint_as_float(b1.y); hi1 = __uint_as_float(b2.x); hi2 = __uint_as_float(b2.y);
       ref = rm.x; meta = rm.y;
     } else {
-      const uint4 q0 = ldg4(a.nodes + 2 * (size_t)cur), q1 = ldg4(a.nodes + 2 * (size_t)cur + 1);
+      uint4 q0, q1;
+      ldg8(a.nodes + 2 * (size_t)cur, q0, q1);
       lo0 = __uint_as_float(q0.x); lo1 = __uint_as_float(q0.y); lo2 = __uint_as_float(q0.z);
       hi0 = __uint_as_float(q0.w); hi1 = __uint_as_float(q1.x); hi2 = __uint_as_float(q1.y);
       ref = q1.z; meta = q1.w;
