@@ -129,7 +129,9 @@ typedef struct {
  *  threads_per_block : CTA size (multiple of 32, <= 1024; default 256).
  *  ctas_per_sm       : persistent CTAs per SM (default: from occupancy).
  *  reg_stack         : reserved (0).
- *  smem_stack        : shared-memory stack entries per thread (default 16).
+ *  smem_stack        : shared-memory stack entries per thread (default 16,
+ *                      at most 64; own-box bvh2 layouts other than the shared
+ *                      slab round it down to a power of two).
  *  ordered_children  : 0 or 1 = children sorted by entry distance
  *                      (closest hit), 2 = stored slot order, 3 = nearest
  *                      child first and the others in slot order.

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kMaxThreadsPerBlock)
   st.sh = smem + threadIdx.x;
   st.stride = blockDim.x;
   st.cap_sh = (int)smem_stack;
-  st.sp = 0;
+  st.reset();
   Counts cnt;
   const uint32_t lane = threadIdx.x & 31u;
   while (true) {
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kMaxThreadsPerBlock)
     L.steps = 0;
     L.err = 0;
     L.found = false;
-    st.sp = 0;
+    st.reset();
     L.cur = S.family == kFamilyBin ? (a.n_nodes > 0 ? 0u : kEmptyRef) : a.root_ref;
     switch (S.family) {
       case kFamilyBin: trace_one<true, 2, PREC_F32, LAYOUT_AOS>(a, L, st, cnt); break;

@@ -358,7 +358,7 @@ __device__ __forceinline__ void cpq_kernel_body(const TraceArgs &a) {
   st.sh = smem_stack + threadIdx.x;
   st.stride = blockDim.x;
   st.cap_sh = (int)a.smem_stack;
-  st.sp = 0;
+  st.reset();
   Counts cnt;
   uint32_t n_pts = 0;
   const uint32_t lane = threadIdx.x & 31u;
@@ -376,7 +376,7 @@ __device__ __forceinline__ void cpq_kernel_body(const TraceArgs &a) {
     L.b = CpBest{__int_as_float(0x7f800000), 0.f, 0.f, SCION_PRIM_MISS};
     L.steps = 0;
     L.err = 0;
-    st.sp = 0;
+    st.reset();
     // a point that is not finite, or a radius that is not >= 0, finds nothing
     const bool live = isfinite(pt.x) && isfinite(pt.y) && isfinite(pt.z) && pt.w >= 0.0f;
     if constexpr (OWN) L.cur = live && a.n_nodes > 0 ? 0u : kEmptyRef;

@@ -240,39 +240,71 @@ __device__ __forceinline__ uint32_t qword(const uint4 (&q)[NQ], int i) {
 // Entries (ref, entry distance); with TF also the exit distance of the
 // entry's interval (the shared-slab traversal carries intervals, not boxes),
 // in a second shared-memory column.
-template <bool TF>
+template <bool TF, bool RING = false>
 struct StackT {
   uint2 *sh;      // this thread's column in shared memory
   float *shf;     // exit distances (TF)
   int stride;     // blockDim.x
-  int cap_sh;     // entries in shared memory
-  int sp;
+  int cap_sh;     // entries in shared memory (RING: a power of two)
+  int sp;         // entries on the stack
+  int base;       // RING: entries [0, base) are in local memory, [base, sp) in shared memory
   float ptf;      // exit distance of the last popped entry (TF)
   uint2 loc[kLocalStack];
   float locf[TF ? kLocalStack : 1];
 
+  // Without RING the first cap_sh entries live in shared memory and deeper
+  // ones in local memory. With RING the shared part holds the cap_sh most
+  // recent entries: when it is full the oldest one moves to local memory,
+  // which is read again only once the shared part is empty, so pushes and
+  // pops near the top stay in shared memory however deep the stack grows.
+  __device__ __forceinline__ int slot(int i) const { return (RING ? (i & (cap_sh - 1)) : i) * stride; }
+  __device__ __forceinline__ void reset() {
+    sp = 0;
+    base = 0;
+  }
   __device__ __forceinline__ bool push(uint32_t ref, float tn, float tf = 0.f) {
     const uint2 e = make_uint2(ref, __float_as_uint(tn));
-    if (sp < cap_sh) {
-      sh[sp * stride] = e;
-      if (TF) shf[sp * stride] = tf;
-    } else if (sp < cap_sh + kLocalStack) {
-      loc[sp - cap_sh] = e;
-      if (TF) locf[sp - cap_sh] = tf;
+    if constexpr (RING) {
+      if (sp - base == cap_sh) {
+        if (base == kLocalStack) return false;
+        loc[base] = sh[slot(base)];
+        if (TF) locf[base] = shf[slot(base)];
+        ++base;
+      }
+      sh[slot(sp)] = e;
+      if (TF) shf[slot(sp)] = tf;
     } else {
-      return false;
+      if (sp < cap_sh) {
+        sh[sp * stride] = e;
+        if (TF) shf[sp * stride] = tf;
+      } else if (sp < cap_sh + kLocalStack) {
+        loc[sp - cap_sh] = e;
+        if (TF) locf[sp - cap_sh] = tf;
+      } else {
+        return false;
+      }
     }
     ++sp;
     return true;
   }
   __device__ __forceinline__ uint2 pop() {
     --sp;
-    if (sp < cap_sh) {
-      if (TF) ptf = shf[sp * stride];
-      return sh[sp * stride];
+    if constexpr (RING) {
+      if (sp >= base) {
+        if (TF) ptf = shf[slot(sp)];
+        return sh[slot(sp)];
+      }
+      base = sp;
+      if (TF) ptf = locf[sp];
+      return loc[sp];
+    } else {
+      if (sp < cap_sh) {
+        if (TF) ptf = shf[sp * stride];
+        return sh[sp * stride];
+      }
+      if (TF) ptf = locf[sp - cap_sh];
+      return loc[sp - cap_sh];
     }
-    if (TF) ptf = locf[sp - cap_sh];
-    return loc[sp - cap_sh];
   }
 };
 using Stack = StackT<false>;
@@ -381,8 +413,8 @@ struct Lane {
 
 // Next stacked entry that can still hold a closer hit (closest) or any
 // stacked entry (any-hit); kEmptyRef when the stack is exhausted.
-template <bool ANY>
-__device__ __forceinline__ uint32_t pop_next(Stack &st, float best_t, float &tn) {
+template <bool ANY, class S>
+__device__ __forceinline__ uint32_t pop_next(S &st, float best_t, float &tn) {
   while (st.sp > 0) {
     const uint2 e = st.pop();
     tn = __uint_as_float(e.y);
@@ -390,8 +422,8 @@ __device__ __forceinline__ uint32_t pop_next(Stack &st, float best_t, float &tn)
   }
   return kEmptyRef;
 }
-template <bool ANY>
-__device__ __forceinline__ uint32_t pop_next(Stack &st, float best_t) {
+template <bool ANY, class S>
+__device__ __forceinline__ uint32_t pop_next(S &st, float best_t) {
   float tn;
   return pop_next<ANY>(st, best_t, tn);
 }
@@ -601,8 +633,8 @@ __device__ __forceinline__ float eq10_f(uint32_t w, int axis) {
 // PREC selects the box codec: f32 corners, or world-grid codes decoded
 // exactly as the packer verified them (q16: fma(code, step, wlo); eq10: one
 // fused multiply-add rounded outward per coordinate) before the f32 slab test.
-template <int PREC, int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, Stack &st, Counts &cnt) {
+template <int PREC, int SOA, int CREF, bool ANY, bool STATS, class S>
+__device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, S &st, Counts &cnt) {
   const Ray &r = L.r;
   const uint32_t cur = L.cur;
   if (STATS) cnt.nodes++;
@@ -773,7 +805,7 @@ __device__ __forceinline__ void start_ray(const TraceArgs &a, Lane &L) {
 }
 
 template <bool OWN, int PREC>
-using StackFor = StackT<OWN && PREC == PREC_SLAB>;
+using StackFor = StackT<OWN && PREC == PREC_SLAB, OWN && PREC != PREC_SLAB>;
 
 // ------------------------------------------------------------------ kernel body
 // Trace one ray to completion with the layout's step function.
@@ -817,7 +849,7 @@ __device__ __forceinline__ void body_warp_batch(const TraceArgs &a, S &st) {
     L.steps = 0;
     L.err = 0;
     L.found = false;
-    st.sp = 0;
+    st.reset();
     start_ray<OWN, PREC>(a, L);
     if (STATS) n_rays++;
     trace_lane<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, L, st, cnt);
@@ -889,7 +921,7 @@ __device__ __forceinline__ void body_refill(const TraceArgs &a, S &st) {
           L.steps = 0;
           L.err = 0;
           L.found = false;
-          st.sp = 0;
+          st.reset();
           start_ray<OWN, PREC>(a, L);
           has_ray = true;
           if (STATS) n_rays++;
@@ -938,7 +970,7 @@ __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
   st.shf = reinterpret_cast<float *>(smem_stack + blockDim.x * a.smem_stack) + threadIdx.x;
   st.stride = blockDim.x;
   st.cap_sh = (int)a.smem_stack;
-  st.sp = 0;
+  st.reset();
   if (a.refill_min) body_refill<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, st);
   else body_warp_batch<OWN, W, PREC, SOA, CREF, ANY, STATS>(a, st);
 }
