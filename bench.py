@@ -266,11 +266,13 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
     return step, per, modes, [t for _, t in picks]
 
 
-def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("warp_batch",) * 3):
-    """The same step through the public API from pinned host memory: every
-    step copies its rays host->device and its results device->host, pipelined
-    in chunks on three streams (scion.HostTracer) so that the copies overlap
-    the traversal; bounce and shadow traces start after the primary traces."""
+def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("warp_batch",) * 3, zero_copy=True):
+    """The same step through the public API from pinned host memory; bounce
+    and shadow traces start after the primary traces. zero_copy: the kernels
+    read each step's rays from, and write its results to, the pinned host
+    buffers over the host link (no staging copies); otherwise every step
+    copies its rays host->device and its results device->host, pipelined in
+    chunks on three streams so that the copies overlap the traversal."""
     h_in = [torch.from_numpy(r).pin_memory() for r in host_rays]
     n = [r.shape[0] for r in host_rays]
     h_out = [torch.empty((n[0], 4), dtype=torch.int32).pin_memory(),
@@ -279,7 +281,7 @@ def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("w
     ps = [FETCH_MODES[m] or None for m in modes]
     jobs = [(bvh, h_in[0], h_out[0], "closest", ps[0]), (bvh, h_in[1], h_out[1], "closest", ps[1]),
             (bvh, h_in[2], h_out[2], "any", ps[2])]
-    tracer = scion.HostTracer()
+    tracer = scion.HostTracer(zero_copy=zero_copy)
     stream = torch.cuda.current_stream()
     phases = [[0], [1, 2]]  # bounce and shadow rays come from the primary hits
     for _ in range(warmup):
@@ -843,13 +845,19 @@ def main():
     fm = r["fetch_mode"]
     e2e_t, bi, bo = e2e_layout(scion, torch, r["_bvh"], (prim, bounce, shadow), args.steps, args.warmup, flush_buf,
                                (fm["primary"], fm["bounce"], fm["shadow"]))
-    e2e_ms = trimmed_mean(e2e_t)
+    staged_t, _, _ = e2e_layout(scion, torch, r["_bvh"], (prim, bounce, shadow), args.steps, args.warmup,
+                                flush_buf, (fm["primary"], fm["bounce"], fm["shadow"]), zero_copy=False)
+    e2e_ms, staged_ms = trimmed_mean(e2e_t), trimmed_mean(staged_t)
     if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
+        t = torch.tensor([e2e_ms, staged_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms, staged_ms = float(t[0].item()), float(t[1].item())
     e2e = {"value": world * sum(n_rays) / (e2e_ms / 1e3) / 1e6, "unit": "Mrays/s",
-           "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
+           "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms,
+           "transfer": "in place: the trace kernels read each step's rays from and write its results to "
+                       "pinned host memory over NVLink-C2C (scion.HostTracer(zero_copy=True))",
+           "staged_copies": {"value": world * sum(n_rays) / (staged_ms / 1e3) / 1e6, "ms_per_step": staged_ms,
+                             "how": "cudaMemcpyAsync of 1M-ray chunks on three streams overlapping the traces"}}
     for v in results.values():
         v.pop("_bvh", None)
     extra = {"pareto_coherent": pareto({k: (v["bvh_mb"], v["mrays_s"]) for k, v in results.items()})}

@@ -247,14 +247,19 @@ scion_status scion_bvh_info(scion_bvh bvh, uint64_t *node_bytes, uint64_t *prim_
                             uint32_t *depth, uint32_t *n_nodes);
 
 /* Closest hit of each ray (Fig. 4 closest_hit; ties at equal t go to the
- * lowest triangle index). d_rays: device scion_ray[n]; d_hits: device
- * scion_hit[n]. params: NULL for defaults. n = 0 is a no-op. */
+ * lowest triangle index). d_rays: scion_ray[n]; d_hits: scion_hit[n]; each in
+ * device memory or in page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister), which the kernel then reads or writes in place over the
+ * host link, with no staging copy; results in host memory are complete once
+ * `stream` has reached the end of the call. Pageable host memory:
+ * SCION_ERR_INVALID_ARG, before any launch. params: NULL for defaults. n = 0
+ * is a no-op. */
 scion_status scion_trace_closest(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
                                  scion_hit *d_hits, const scion_trace_params *params,
                                  scion_stream stream);
 
 /* Any hit: d_occluded[i] = 1 iff ray i has an accepted hit in [tmin, tmax],
- * else 0 (device uint32[n]). */
+ * else 0 (uint32[n]). Buffers as for scion_trace_closest. */
 scion_status scion_trace_any(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
                              uint32_t *d_occluded, const scion_trace_params *params,
                              scion_stream stream);
@@ -285,8 +290,9 @@ scion_status scion_trace_backward(scion_bvh bvh, const scion_ray *d_rays, const 
  * every layout). Node boxes are bounded from below with outward rounding, so
  * no box that could hold the winner is skipped; the paper's "distmax" bound
  * update is not used.
- *  d_points : device scion_point[n] (16-byte aligned).
- *  d_out    : device scion_closest_point[n] (16-byte aligned).
+ *  d_points : scion_point[n] (16-byte aligned), device or page-locked host
+ *             memory as for scion_trace_closest.
+ *  d_out    : scion_closest_point[n] (16-byte aligned), likewise.
  *  params   : as scion_trace_closest (ordered_children: 0/1 children sorted
  *             by box distance, 2 slot order, 3 nearest first); rays_per_fetch
  *             must be 0 or 32.

@@ -105,6 +105,25 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The address a kernel uses for a ray or result buffer: device (or managed)
+// memory as given, page-locked host memory through its device mapping (the
+// kernel then reads and writes host memory directly, e.g. over NVLink-C2C).
+// Pageable host memory is not reachable from a kernel: nullptr.
+const void *kernel_view(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    // the mapping of the allocation's start, shifted to p
+    const char *base = static_cast<const char *>(at.hostPointer);
+    return static_cast<const char *>(at.devicePointer) + (static_cast<const char *>(p) - base);
+  }
+  return nullptr;
+}
+
 template <typename T>
 scion_status upload(void **dst, const std::vector<T> &src, cudaStream_t s, uint64_t *bytes) {
   *bytes = src.size() * sizeof(T);
@@ -357,8 +376,13 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
   TraceArgs a;
   bvh_args(b, a);
-  a.rays = reinterpret_cast<const float4 *>(rays);
-  a.out = out;
+  const void *k_rays = kernel_view(rays), *k_out = kernel_view(out);
+  if (!k_rays || !k_out) {
+    g_last_error = "ray and result buffers must be device memory or page-locked host memory";
+    return SCION_ERR_INVALID_ARG;
+  }
+  a.rays = reinterpret_cast<const float4 *>(k_rays);
+  a.out = const_cast<void *>(k_out);
   a.n = n;
   a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
   a.ordered = ordered;

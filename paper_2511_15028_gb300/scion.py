@@ -322,14 +322,29 @@ def _params(params):
     return ctypes.byref(TraceParams(**params))
 
 
-def scion_trace_closest(bvh: BVH, rays, hits=None, params=None, stream=None):
-    """Closest hits of device rays (float32 [n, 8]); returns int32 [n, 4]
-    holding (t, u, v) as float bits and prim as uint32 bits."""
+def _ray_buffer(t, dtype):
+    """Device tensors, or pinned host tensors that the kernel reads and
+    writes in place."""
+    assert (t.is_cuda or t.is_pinned()) and t.dtype == dtype and t.is_contiguous()
+
+
+def _like(rays, shape, dtype):
     import torch
-    assert rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous()
+    if rays.is_cuda:
+        return torch.empty(shape, dtype=dtype, device=rays.device)
+    return torch.empty(shape, dtype=dtype).pin_memory()
+
+
+def scion_trace_closest(bvh: BVH, rays, hits=None, params=None, stream=None):
+    """Closest hits of rays (float32 [n, 8], on the device or in pinned host
+    memory); returns int32 [n, 4] beside them holding (t, u, v) as float bits
+    and prim as uint32 bits."""
+    import torch
+    _ray_buffer(rays, torch.float32)
     n = rays.shape[0]
     if hits is None:
-        hits = torch.empty((n, 4), dtype=torch.int32, device=rays.device)
+        hits = _like(rays, (n, 4), torch.int32)
+    _ray_buffer(hits, torch.int32)
     _check(lib().scion_trace_closest(bvh.handle, ctypes.c_void_p(rays.data_ptr()), n,
                                      ctypes.c_void_p(hits.data_ptr()), _params(params),
                                      _stream_ptr(stream)), "scion_trace_closest")
@@ -337,12 +352,14 @@ def scion_trace_closest(bvh: BVH, rays, hits=None, params=None, stream=None):
 
 
 def scion_trace_any(bvh: BVH, rays, occluded=None, params=None, stream=None):
-    """Any-hit flags (int32 [n]: 1 occluded, 0 clear) of device rays."""
+    """Any-hit flags (int32 [n]: 1 occluded, 0 clear) of rays on the device or
+    in pinned host memory."""
     import torch
-    assert rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous()
+    _ray_buffer(rays, torch.float32)
     n = rays.shape[0]
     if occluded is None:
-        occluded = torch.empty((n,), dtype=torch.int32, device=rays.device)
+        occluded = _like(rays, (n,), torch.int32)
+    _ray_buffer(occluded, torch.int32)
     _check(lib().scion_trace_any(bvh.handle, ctypes.c_void_p(rays.data_ptr()), n,
                                  ctypes.c_void_p(occluded.data_ptr()), _params(params),
                                  _stream_ptr(stream)), "scion_trace_any")
@@ -502,11 +519,20 @@ class HostTracer:
     chunk overlap the traversal of the others. Device staging buffers are
     allocated once (on first use) and reused."""
 
-    def __init__(self, n_streams: int = 3, chunk_rays: int = 1 << 20):
+    def __init__(self, n_streams: int = 3, chunk_rays: int = 1 << 20, first_chunk_rays: int = 0,
+                 zero_copy: bool = False):
+        """first_chunk_rays: size of the first chunk (0: chunk_rays); the
+        following chunks of the first phase double up to chunk_rays, so tracing
+        starts after a short copy while later chunks are large. (The copies of
+        later phases are issued early and overlap the earlier traces.)"""
         import torch
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.join = torch.cuda.Stream()
         self.chunk = chunk_rays
+        self.first = first_chunk_rays or chunk_rays
+        # zero_copy: no staging copies; each job is one launch that reads its
+        # rays from and writes its results to the pinned host buffers directly
+        self.zero_copy = zero_copy
         self._rays = [None] * n_streams
         self._outs = [None] * n_streams
 
@@ -536,15 +562,21 @@ class HostTracer:
             s.wait_stream(cur)
         if phases is None:
             phases = [list(range(len(jobs)))]
+        if self.zero_copy:
+            self._trace_in_place(jobs, phases, cur)
+            return
         k = 0
         prev_done = None
         for pi, ph in enumerate(phases):
             traced = []
+            size = self.first if pi == 0 else self.chunk  # later phases' copies run ahead
             for j in ph:
                 bvh, h_rays, h_out, query, params = jobs[j]
                 n = h_rays.shape[0]
-                for b in range(0, n, self.chunk):
-                    e = min(n, b + self.chunk)
+                b = 0
+                while b < n:
+                    e = min(n, b + size)
+                    size = min(self.chunk, 2 * size)
                     i = k % len(self.streams)
                     s = self.streams[i]
                     with torch.cuda.stream(s):
@@ -564,6 +596,36 @@ class HostTracer:
                             traced.append(ev)
                         h_out[b:e].copy_(d_o, non_blocking=True)
                     k += 1
+                    b = e
+            if traced:
+                for ev in traced:
+                    self.join.wait_event(ev)
+                prev_done = torch.cuda.Event()
+                prev_done.record(self.join)
+        for s in self.streams:
+            cur.wait_stream(s)
+
+    def _trace_in_place(self, jobs, phases, cur):
+        import torch
+        k = 0
+        prev_done = None
+        for pi, ph in enumerate(phases):
+            traced = []
+            for j in ph:
+                bvh, h_rays, h_out, query, params = jobs[j]
+                s = self.streams[k % len(self.streams)]
+                k += 1
+                with torch.cuda.stream(s):
+                    if prev_done is not None:
+                        s.wait_event(prev_done)
+                    if query == "closest":
+                        scion_trace_closest(bvh, h_rays, h_out, params=params, stream=s)
+                    else:
+                        scion_trace_any(bvh, h_rays, h_out, params=params, stream=s)
+                    if pi + 1 < len(phases):
+                        ev = torch.cuda.Event()
+                        ev.record(s)
+                        traced.append(ev)
             if traced:
                 for ev in traced:
                     self.join.wait_event(ev)

@@ -1,5 +1,6 @@
 """GPU parity: every layout's closest-hit and any-hit results match the CPU
 oracle bit for bit (hit/miss, prim, t, u, v), through the C ABI."""
+import ctypes
 import math
 
 import numpy as np
@@ -278,4 +279,39 @@ def test_concurrent_streams_same_bvh_and_host_tracer(sc_mod, oracle_mod):
         assert_same_hits(sc_mod.split_hits(h_o), exp, f"host tracer {p} {phases}")
         assert_same_hits(sc_mod.split_hits(h_o2), exp, f"host tracer {p} {phases}")
         assert np.array_equal(h_a.numpy().astype(np.uint32), eocc)
+    # no staging copies: the kernels read rays from and write results to the
+    # pinned host buffers in place, phases ordered by events
+    direct = sc_mod.HostTracer(n_streams=2, zero_copy=True)
+    for phases in (None, [[1], [0, 2]]):
+        h_o.fill_(0)
+        h_o2.fill_(0)
+        h_a.fill_(7)
+        direct.trace([(bvh, h_r, h_o, "closest", None), (bvh, h_s, h_a, "any", None),
+                      (bvh, h_r, h_o2, "closest", dict(rays_per_fetch=8))], phases)
+        torch.cuda.synchronize()
+        assert_same_hits(sc_mod.split_hits(h_o), exp, f"in place {phases}")
+        assert_same_hits(sc_mod.split_hits(h_o2), exp, f"in place {phases}")
+        assert np.array_equal(h_a.numpy().astype(np.uint32), eocc)
+    got = sc_mod.scion_trace_closest(bvh, h_r)  # pinned in, pinned out
+    torch.cuda.synchronize()
+    assert not got.is_cuda and got.is_pinned()
+    assert_same_hits(sc_mod.split_hits(got), exp, "pinned host buffers")
+    # pageable host memory cannot be reached from a kernel: rejected before any launch
+    L = sc_mod.lib()
+    pageable = np.ascontiguousarray(rays[:64])
+    d_out = torch.empty((64, 4), dtype=torch.int32, device="cuda")
+    st = L.scion_trace_closest(bvh.handle, ctypes.c_void_p(pageable.ctypes.data), 64,
+                               ctypes.c_void_p(d_out.data_ptr()), None, None)
+    assert st == 1
+    st = L.scion_trace_any(bvh.handle, ctypes.c_void_p(d.data_ptr()), 64,
+                           ctypes.c_void_p(np.zeros(64, np.int32).ctypes.data), None, None)
+    assert st == 1
+    # a growing chunk size (7,000 rays first, doubling up to 30,000)
+    ramp = sc_mod.HostTracer(n_streams=2, chunk_rays=30_000, first_chunk_rays=7_000)
+    h_o.fill_(0)
+    h_a.fill_(7)
+    ramp.trace([(bvh, h_r, h_o, "closest", None), (bvh, h_s, h_a, "any", None)], [[0], [1]])
+    torch.cuda.synchronize()
+    assert_same_hits(sc_mod.split_hits(h_o), exp, "host tracer, growing chunks")
+    assert np.array_equal(h_a.numpy().astype(np.uint32), eocc)
     assert sc_mod.scion_get_status(bvh) == 0
