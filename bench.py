@@ -184,15 +184,25 @@ FETCH_MODES = {"warp_batch": {}, "refill1": {"rays_per_fetch": 1}, "refill8": {"
                "warp_batch/nearest_first": {"ordered_children": 3},
                "refill1/nearest_first": {"rays_per_fetch": 1, "ordered_children": 3},
                "refill8/nearest_first": {"rays_per_fetch": 8, "ordered_children": 3}}
+# Primary rays are a row-major 1920-wide image: warps can take 8x4 pixel tiles.
+PRIMARY_RASTER = 1920
+RASTER_MODES = {"tiles": {"raster_width": PRIMARY_RASTER},
+                "tiles/nearest_first": {"raster_width": PRIMARY_RASTER, "ordered_children": 3}}
 
 
-def pick_fetch(scion, torch, bvh, fn, rays, out, reps=3):
+def mode_params(name):
+    return (FETCH_MODES[name] if name in FETCH_MODES else RASTER_MODES[name]) or None
+
+
+def pick_fetch(scion, torch, bvh, fn, rays, out, reps=3, extra=None):
     """Traversal parameters chosen by measurement (the autotuner's choice for
     one layout and one kind of ray): the fastest candidate, and every
     candidate's best time in ms."""
     best, best_t, trials = None, None, {}
     cands = FETCH_MODES if fn is scion.scion_trace_closest else {
         k: v for k, v in FETCH_MODES.items() if "nearest" not in k}
+    if extra:
+        cands = {**cands, **extra}
     for name, p in cands.items():
         fn(bvh, rays, out, params=p or None)
         torch.cuda.synchronize()
@@ -211,7 +221,7 @@ def pick_fetch(scion, torch, bvh, fn, rays, out, reps=3):
     return best, trials
 
 
-def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler=None):
+def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler=None, fixed=None):
     """K timed steps of primary closest hit, then bounce closest hit and
     shadow any hit (both made from the primary hits, so they wait for it and
     run concurrently on two streams). Events on each launch's own stream
@@ -221,9 +231,13 @@ def time_layout(scion, torch, bvh, rays, outs, steps, warmup, flush_buf, sampler
     d_p, d_b, d_s = rays
     o_p, o_b, o_s = outs
     fns = (scion.scion_trace_closest, scion.scion_trace_closest, scion.scion_trace_any)
-    picks = [pick_fetch(scion, torch, bvh, f, r, o) for f, r, o in zip(fns, rays, outs)]
+    if fixed:  # modes given on the command line: no trials
+        picks = [(m, {}) for m in fixed]
+    else:
+        picks = [pick_fetch(scion, torch, bvh, f, r, o, extra=RASTER_MODES if i == 0 else None)
+                 for i, (f, r, o) in enumerate(zip(fns, rays, outs))]
     modes = [m for m, _ in picks]
-    ps = [FETCH_MODES[m] or None for m in modes]
+    ps = [mode_params(m) for m in modes]
     stream = torch.cuda.current_stream()
     s_b, s_s = torch.cuda.Stream(), torch.cuda.Stream()
 
@@ -278,7 +292,7 @@ def e2e_layout(scion, torch, bvh, host_rays, steps, warmup, flush_buf, modes=("w
     h_out = [torch.empty((n[0], 4), dtype=torch.int32).pin_memory(),
              torch.empty((n[1], 4), dtype=torch.int32).pin_memory(),
              torch.empty((n[2],), dtype=torch.int32).pin_memory()]
-    ps = [FETCH_MODES[m] or None for m in modes]
+    ps = [mode_params(m) for m in modes]
     jobs = [(bvh, h_in[0], h_out[0], "closest", ps[0]), (bvh, h_in[1], h_out[1], "closest", ps[1]),
             (bvh, h_in[2], h_out[2], "any", ps[2])]
     tracer = scion.HostTracer(zero_copy=zero_copy)
@@ -707,6 +721,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--layouts", default="all", help="all | comma-separated sweep names")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fetch", default=None,
+                    help="primary,bounce,shadow fetch modes (names of FETCH_MODES / RASTER_MODES); skips the "
+                         "per-layout trials, e.g. to profile exactly the modes a plain run chose")
     ap.add_argument("--no-extra", action="store_true", help="skip the incoherent, batched and backward measurements")
     ap.add_argument("--section", default="all", choices=["all", "incoherent", "build", "cpq"],
                     help="incoherent: only the 2^23-triangle section (for profiling); "
@@ -799,8 +816,9 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+        fixed = args.fetch.split(",") if args.fetch else None
         step, per, modes, trials = time_layout(scion, torch, bvh, rays, outs, args.steps, args.warmup, flush_buf,
-                                               sampler)
+                                               sampler, fixed)
         ms = trimmed_mean(step.tolist())
         if dist is not None:
             t = torch.tensor([ms], device=dev)

@@ -144,10 +144,17 @@ typedef struct {
  *                      Results are identical; which is faster depends on the
  *                      layout and the rays. Above 32: SCION_ERR_INVALID_ARG.
  *  max_steps         : per-ray node+leaf visit limit (0 = derived from size).
- *  reserved          : must be 0. */
+ *  raster_width      : 0, or the rays are a row-major image this many rays
+ *                      wide (ray i is pixel (i mod w, i / w); the last row
+ *                      may be partial): each warp then traces an 8 x 4 pixel
+ *                      tile instead of 32 consecutive rays, which keeps camera
+ *                      rays of one warp close together. Warp batches only
+ *                      (rays_per_fetch 0 or 32), rays only (not closest point
+ *                      queries), not in batched launches; otherwise
+ *                      SCION_ERR_INVALID_ARG. Results are identical. */
 typedef struct {
   uint32_t threads_per_block, ctas_per_sm, reg_stack, smem_stack, ordered_children,
-      rays_per_fetch, max_steps, reserved;
+      rays_per_fetch, max_steps, raster_width;
 } scion_trace_params;
 
 /* A closest point query (App. G "Closest Point Query"): a point and a squared

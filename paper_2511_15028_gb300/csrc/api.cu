@@ -162,6 +162,18 @@ uint32_t stack_entries(scion_bvh b, uint32_t requested, bool ray_query) {
   return p;
 }
 
+// Warp-batch work of a launch over a.n rays: consecutive 32-ray batches, or
+// 8x4 pixel tiles of a row-major image raster_w wide (32 slots per tile).
+void set_raster(TraceArgs &a, uint32_t raster_w) {
+  a.raster_w = raster_w;
+  if (!raster_w) {
+    a.n_work = a.n;
+    return;
+  }
+  const unsigned long long rows = (a.n + raster_w - 1) / raster_w;
+  a.n_work = ((raster_w + 7ull) / 8) * ((rows + 3) / 4) * 32ull;
+}
+
 // Query kinds of launch_trace.
 constexpr int kQueryClosest = 0, kQueryAny = 1, kQueryPoint = 2;
 
@@ -347,8 +359,11 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
     return SCION_ERR_INVALID_ARG;
   scion_trace_params p{};
   if (params) p = *params;
-  if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch > 32)
+  if (p.reg_stack != 0 || p.rays_per_fetch > 32) return SCION_ERR_INVALID_ARG;
+  if (p.raster_width != 0 && ((p.rays_per_fetch != 0 && p.rays_per_fetch != 32) || query == kQueryPoint)) {
+    g_last_error = "raster_width needs warp batches (rays_per_fetch 0 or 32) and rays";
     return SCION_ERR_INVALID_ARG;
+  }
   if (query == kQueryPoint && p.rays_per_fetch != 0 && p.rays_per_fetch != 32) {
     g_last_error = "closest point queries take 32-point warp batches only (rays_per_fetch 0 or 32)";
     return SCION_ERR_INVALID_ARG;
@@ -388,6 +403,7 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   a.ordered = ordered;
   a.smem_stack = smem_entries;
   a.refill_min = p.rays_per_fetch < 32 ? p.rays_per_fetch : 0u;
+  set_raster(a, p.raster_width);
   const int slot = stream_slot(b, stream);
   if (slot < 0) {
     g_last_error = "more than 64 streams have traced this BVH";
@@ -750,7 +766,7 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
     scion_bvh b = bvhs[i];
     scion_trace_params p{};
     if (per_scene) p = per_scene[i];
-    if (!b || (n[i] > 0 && (!d_rays[i] || !d_hits[i])) || p.ordered_children > 3 ||
+    if (!b || (n[i] > 0 && (!d_rays[i] || !d_hits[i])) || p.ordered_children > 3 || p.raster_width != 0 ||
         (reinterpret_cast<uintptr_t>(d_rays[i]) & 15u) || (reinterpret_cast<uintptr_t>(d_hits[i]) & 15u)) {
       delete bt;
       return SCION_ERR_INVALID_ARG;
@@ -1034,8 +1050,8 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
     return SCION_ERR_INVALID_ARG;
   scion_trace_params p{};
   if (params) p = *params;
-  if (p.reserved != 0 || p.reg_stack != 0 || p.rays_per_fetch > 32 ||
-      p.ordered_children > 3)
+  if (p.reg_stack != 0 || p.rays_per_fetch > 32 || p.ordered_children > 3 ||
+      (p.raster_width != 0 && p.rays_per_fetch != 0 && p.rays_per_fetch != 32))
     return SCION_ERR_INVALID_ARG;
   const uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
@@ -1070,6 +1086,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   a.ordered = order_mode(p.ordered_children);
   a.smem_stack = smem_entries;
   a.refill_min = p.rays_per_fetch < 32 ? p.rays_per_fetch : 0u;
+  set_raster(a, p.raster_width);
   a.work = static_cast<unsigned long long *>(scratch);
   a.exit_count = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(scratch) + 8);
   a.status = b->d_scratch + 3;  // device errors still go to the BVH's status word

@@ -46,6 +46,8 @@ struct TraceArgs {
   uint32_t ordered;         // 0 slot order, 1 sorted by entry distance, 2 nearest first
   uint32_t smem_stack;      // shared-memory stack entries per thread
   uint32_t refill_min;      // 0: 32-ray warp batches; k: refill once k lanes idle
+  uint32_t raster_w;        // 0, or rays form a row-major image this wide: warp batches are 8x4 tiles
+  unsigned long long n_work;  // warp-batch slots: n, or 32 per tile of the image
   unsigned long long *work; // persistent work counter (self-resetting)
   uint32_t *exit_count;     // CTAs finished (self-resetting)
   uint32_t *status;         // first device error code
@@ -839,8 +841,14 @@ __device__ __forceinline__ void body_warp_batch(const TraceArgs &a, S &st) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.work, 32ull);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (base >= a.n) break;
-    const unsigned long long rid = base + lane;
+    if (base >= a.n_work) break;
+    unsigned long long rid = base + lane;
+    if (a.raster_w) {
+      // slot batch t is the 8x4 pixel tile (t mod tiles_x, t / tiles_x)
+      const unsigned long long t = base >> 5, tiles_x = (a.raster_w + 7u) >> 3;
+      const unsigned long long px = (t % tiles_x) * 8u + (lane & 7u), py = (t / tiles_x) * 4u + (lane >> 3);
+      rid = px < a.raster_w ? py * a.raster_w + px : a.n;
+    }
     if (rid >= a.n) continue;
     Lane L;
     L.rid = rid;

@@ -42,7 +42,7 @@ class LayoutDesc(ctypes.Structure):
 class TraceParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "threads_per_block", "ctas_per_sm", "reg_stack", "smem_stack", "ordered_children",
-        "rays_per_fetch", "max_steps", "reserved")]
+        "rays_per_fetch", "max_steps", "raster_width")]
 
 
 class DebugInfo(ctypes.Structure):

@@ -73,6 +73,12 @@ def test_config1_every_layout_bit_exact(sc_mod, config1, kw):
     assert_same_hits(lane, exp, "refill 13")
     nearest = gpu_closest(sc_mod, bvh, rays, params=dict(ordered_children=3))
     assert_same_hits(nearest, exp, "nearest first")
+    # the rays are a 128 x 128 raster: 8x4 pixel tiles per warp; also widths
+    # that leave ragged tiles on the right edge and a partial last row
+    for w in (128, 100, 7, 1):
+        tiled = gpu_closest(sc_mod, bvh, rays, params=dict(raster_width=w, ordered_children=3))
+        assert_same_hits(tiled, exp, f"raster {w}")
+        assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(raster_width=w)), occ)
     assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(rays_per_fetch=1)), occ)
     assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(rays_per_fetch=31)), occ)
     assert sc_mod.scion_get_status(bvh) == 0
@@ -170,6 +176,8 @@ def test_device_errors_are_reported_not_faulted(sc_mod):
     assert np.any(got["prim"] == 0xFFFFFFFE) and sc_mod.scion_get_status(bvh) == 6
     with pytest.raises(sc_mod.ScionError):
         gpu_closest(sc_mod, bvh, rays, params=dict(rays_per_fetch=33))
+    with pytest.raises(sc_mod.ScionError):  # tiles need warp batches
+        gpu_closest(sc_mod, bvh, rays, params=dict(raster_width=128, rays_per_fetch=8))
     # a chain: triangles at x = 4^k (k = -50..49) whose two-bin SAH tree peels
     # one triangle per level (depth 100); a ray along +x through all of them
     # pushes one far child per level, more than the 64-entry stack holds
