@@ -104,3 +104,15 @@ def test_batched_mixed_layouts_fall_back_per_scene(mods, oracle_mod):
     for i, (sc, r) in enumerate(wl):
         exp = oracle_mod.BVH2(sc.triangles()).closest(r)
         assert scion.split_hits(hits[i]).tobytes() == exp.tobytes(), i
+
+
+def test_batched_rejects_camera_ray_tiles(mods):
+    """raster_width is a plain-launch parameter: a batch asked for it fails
+    at creation, before any launch."""
+    scion, _ = mods
+    wl = scenes.config4_workload(seed=78, n_scenes=2, scale=0.01)
+    bvhs = [scion.scion_build(sc.verts, scion.layout(width=4, box_layout="soa"), sc.indices) for sc, _ in wl]
+    rays = [torch.from_numpy(r).cuda() for _, r in wl]
+    with pytest.raises(scion.ScionError) as e:
+        scion.Batch(bvhs, rays, params=[dict(raster_width=64), {}])
+    assert e.value.status == 1

@@ -82,3 +82,13 @@ def test_noalloc_rejects_oversize_and_bad_arguments(sc_mod):
     assert st == 1 and "2^62" in scion.last_error()
     assert L.scion_trace_closest_noalloc(None, None, 5, None, None, s) == 1
     assert L.scion_trace_closest_noalloc(bvh.handle, ctypes.c_void_p(rays.data_ptr()), 0, None, None, s) == 0
+    # camera-ray tiles: same hits as 32 consecutive rays; refilled warps cannot take tiles
+    ref = scion.scion_trace_closest(bvh, rays)
+    tiles = scion.TraceParams(raster_width=128)
+    st = L.scion_trace_closest_noalloc(bvh.handle, ctypes.c_void_p(rays.data_ptr()), rays.shape[0],
+                                       ctypes.c_void_p(hits.data_ptr()), ctypes.byref(tiles), s)
+    torch.cuda.synchronize()
+    assert st == 0 and torch.equal(hits, ref)
+    bad = scion.TraceParams(raster_width=128, rays_per_fetch=4)
+    assert L.scion_trace_closest_noalloc(bvh.handle, ctypes.c_void_p(rays.data_ptr()), rays.shape[0],
+                                         ctypes.c_void_p(hits.data_ptr()), ctypes.byref(bad), s) == 1
