@@ -170,8 +170,11 @@ void set_raster(TraceArgs &a, uint32_t raster_w) {
     a.n_work = a.n;
     return;
   }
-  const unsigned long long rows = (a.n + raster_w - 1) / raster_w;
-  a.n_work = ((raster_w + 7ull) / 8) * ((rows + 3) / 4) * 32ull;
+  // up to the last tile holding a ray: ray n-1 is pixel (c, r); every tile of
+  // its tile row holds a ray when a row above r lies in that tile row,
+  // otherwise only the tiles up to column c do
+  const unsigned long long tiles_x = (raster_w + 7ull) / 8, r = (a.n - 1) / raster_w, c = (a.n - 1) % raster_w;
+  a.n_work = ((r / 4) * tiles_x + (r % 4 ? tiles_x : c / 8 + 1)) * 32ull;
 }
 
 // Query kinds of launch_trace.

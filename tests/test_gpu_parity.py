@@ -75,7 +75,7 @@ def test_config1_every_layout_bit_exact(sc_mod, config1, kw):
     assert_same_hits(nearest, exp, "nearest first")
     # the rays are a 128 x 128 raster: 8x4 pixel tiles per warp; also widths
     # that leave ragged tiles on the right edge and a partial last row
-    for w in (128, 100, 7, 1):
+    for w in (128, 100, 7, 1, 1 << 20):
         tiled = gpu_closest(sc_mod, bvh, rays, params=dict(raster_width=w, ordered_children=3))
         assert_same_hits(tiled, exp, f"raster {w}")
         assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(raster_width=w)), occ)
