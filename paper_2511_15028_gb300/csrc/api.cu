@@ -152,11 +152,17 @@ void bvh_args(const scion_bvh b, TraceArgs &a) {
 // default limit of 48 KB also covers the kernels' static shared memory).
 constexpr size_t kSmemOptIn = 32 * 1024;
 
+// Query kinds of launch_trace.
+constexpr int kQueryClosest = 0, kQueryAny = 1, kQueryPoint = 2;
+
 // Shared-memory stack entries per thread. The own-box bvh2 kernels (all but
-// the shared-slab one) keep the shared part of the stack as a ring indexed
-// with a mask, so for them the count is rounded down to a power of two.
-uint32_t stack_entries(scion_bvh b, uint32_t requested, bool ray_query) {
-  if (!(ray_query && b->own_box && b->desc.box_prec != PREC_SLAB)) return requested;
+// the shared-slab one) and the any-hit kernels of nodes up to 4 wide keep the
+// shared part of the stack as a ring indexed with a mask, so for them the
+// count is rounded down to a power of two.
+uint32_t stack_entries(scion_bvh b, uint32_t requested, int query) {
+  const bool ring = query != kQueryPoint && ((b->own_box && b->desc.box_prec != PREC_SLAB) ||
+                                             (!b->own_box && query == kQueryAny && b->desc.width <= 4));
+  if (!ring) return requested;
   uint32_t p = 1;
   while (p * 2 <= requested) p *= 2;
   return p;
@@ -177,8 +183,6 @@ void set_raster(TraceArgs &a, uint32_t raster_w) {
   a.n_work = ((r / 4) * tiles_x + (r % 4 ? tiles_x : c / 8 + 1)) * 32ull;
 }
 
-// Query kinds of launch_trace.
-constexpr int kQueryClosest = 0, kQueryAny = 1, kQueryPoint = 2;
 
 // Shared-memory stack bytes per entry: (ref, entry distance), plus the exit
 // distance for the shared-slab layout, whose traversal carries intervals.
@@ -375,7 +379,7 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
   uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
   if (smem_entries > 64) return SCION_ERR_INVALID_ARG;
-  smem_entries = stack_entries(b, smem_entries, query != kQueryPoint);
+  smem_entries = stack_entries(b, smem_entries, query);
   if (p.ordered_children > 3) return SCION_ERR_INVALID_ARG;
   const uint32_t ordered = order_mode(p.ordered_children);
   TraceKernel k = pick_kernel(b, query, stats ? 1 : 0);
@@ -1059,7 +1063,7 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   const uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
   if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
   if ((p.smem_stack ? p.smem_stack : 16) > 64) return SCION_ERR_INVALID_ARG;
-  const uint32_t smem_entries = stack_entries(b, p.smem_stack ? p.smem_stack : 16, true);
+  const uint32_t smem_entries = stack_entries(b, p.smem_stack ? p.smem_stack : 16, kQueryClosest);
   TraceKernel k = pick_kernel(b, kQueryClosest, 0);
   if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
   void *scratch = nullptr;

@@ -459,8 +459,8 @@ __device__ __forceinline__ void sort_children(float (&t)[W], uint32_t (&r)[W]) {
 // One step of the wide-node traversal: process the entry L.cur (an interior
 // node: test its W child boxes, push the hit ones far to near, continue with
 // the nearest; or a leaf: test its triangles), then pick the next entry.
-template <int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st, Counts &cnt) {
+template <int W, int PREC, int SOA, int CREF, bool ANY, bool STATS, class S>
+__device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Counts &cnt) {
   using N = WideNode<W, PREC, SOA, CREF>;
   const Ray &r = L.r;
   const uint32_t cur = L.cur;
@@ -586,13 +586,13 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, Stack &st
     // push every hit child but the first, last one first; go on with the first
     uint32_t next = kEmptyRef;
     float next_tn = 0.f;
-    if (st.sp + W <= st.cap_sh) {
+    if (st.sp - st.base + W <= st.cap_sh) {
       // room in shared memory for any node: predicated stores, one check
       int sp = st.sp;
 #pragma unroll
       for (int k = W - 1; k >= 0; --k) {
         const bool h = cref[k] != kEmptyRef;
-        if (h && next != kEmptyRef) st.sh[(sp++) * st.stride] = make_uint2(next, __float_as_uint(next_tn));
+        if (h && next != kEmptyRef) st.sh[st.slot(sp++)] = make_uint2(next, __float_as_uint(next_tn));
         next = h ? cref[k] : next;
         next_tn = h ? ctn[k] : next_tn;
       }
@@ -806,8 +806,11 @@ __device__ __forceinline__ void start_ray(const TraceArgs &a, Lane &L) {
   }
 }
 
-template <bool OWN, int PREC>
-using StackFor = StackT<OWN && PREC == PREC_SLAB, OWN && PREC != PREC_SLAB>;
+// The ring pays for its extra register where the kernel has room: the own-box
+// bvh2 kernels (all but the shared slab) and the any-hit kernels of nodes up to
+// 4 wide; in the other 64-register kernels it would spill.
+template <bool OWN, int PREC, int W, bool ANY>
+using StackFor = StackT<OWN && PREC == PREC_SLAB, (OWN && PREC != PREC_SLAB) || (!OWN && ANY && W <= 4)>;
 
 // ------------------------------------------------------------------ kernel body
 // Trace one ray to completion with the layout's step function.
@@ -972,7 +975,7 @@ __device__ __forceinline__ void body_refill(const TraceArgs &a, S &st) {
 template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
 __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
   extern __shared__ uint2 smem_stack[];
-  StackFor<OWN, PREC> st;
+  StackFor<OWN, PREC, W, ANY> st;
   st.sh = smem_stack + threadIdx.x;
   // exit distances (shared-slab layout) follow the entry columns
   st.shf = reinterpret_cast<float *>(smem_stack + blockDim.x * a.smem_stack) + threadIdx.x;
