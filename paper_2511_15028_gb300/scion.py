@@ -328,7 +328,14 @@ def _params(params):
 def _ray_buffer(t, dtype):
     """Device tensors, or pinned host tensors that the kernel reads and
     writes in place."""
-    assert (t.is_cuda or t.is_pinned()) and t.dtype == dtype and t.is_contiguous()
+    if not (t.is_cuda or t.is_pinned()) or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor on the GPU or in pinned host memory, got "
+                        f"{t.dtype} on {t.device}{'' if t.is_contiguous() else ' (not contiguous)'}")
+
+
+def _device_buffer(t, dtype):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor on the GPU, got {t.dtype} on {t.device}")
 
 
 def _like(rays, shape, dtype):
@@ -370,14 +377,15 @@ def scion_trace_any(bvh: BVH, rays, occluded=None, params=None, stream=None):
 
 
 def scion_query_closest_point(bvh: BVH, points, out=None, params=None, stream=None):
-    """Closest points of device query points (float32 [n, 4]: x, y, z,
-    r2max); returns int32 [n, 4] holding (d2, u, v) as float bits and prim as
-    uint32 bits."""
+    """Closest points of query points (float32 [n, 4]: x, y, z, r2max; on
+    the device or in pinned host memory); returns int32 [n, 4] beside them
+    holding (d2, u, v) as float bits and prim as uint32 bits."""
     import torch
-    assert points.is_cuda and points.dtype == torch.float32 and points.is_contiguous()
+    _ray_buffer(points, torch.float32)
     n = points.shape[0]
     if out is None:
-        out = torch.empty((n, 4), dtype=torch.int32, device=points.device)
+        out = _like(points, (n, 4), torch.int32)
+    _ray_buffer(out, torch.int32)
     _check(lib().scion_query_closest_point(bvh.handle, ctypes.c_void_p(points.data_ptr()), n,
                                            ctypes.c_void_p(out.data_ptr()), _params(params),
                                            _stream_ptr(stream)), "scion_query_closest_point")
@@ -388,7 +396,7 @@ def scion_trace_stats(bvh: BVH, rays, query: int = 0, params=None, stream=None):
     """Counting trace: (results, counters) with counters = int64 tensor
     [nodes fetched, leaves visited, triangles tested, rays]."""
     import torch
-    assert rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous()
+    _device_buffer(rays, torch.float32)
     n = rays.shape[0]
     out = (torch.empty((n,), dtype=torch.int32, device=rays.device) if query == 1
            else torch.empty((n, 4), dtype=torch.int32, device=rays.device))

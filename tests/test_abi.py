@@ -69,3 +69,20 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "oracle.h" not in text, f
+
+
+def test_python_binding_rejects_unreachable_buffers_without_gpu():
+    """Ray and result tensors must live on the GPU or in pinned host memory (the
+    kernels read pinned host memory in place); anything else, or the wrong dtype
+    or a strided view, is a TypeError before the library is called."""
+    torch = pytest.importorskip("torch")
+    from paper_2511_15028_gb300 import scion
+    pageable = torch.zeros(4, 8)
+    assert not pageable.is_pinned()
+    cases = [(scion.scion_trace_closest, pageable), (scion.scion_trace_any, pageable),
+             (scion.scion_query_closest_point, torch.zeros(4, 4)), (scion.scion_trace_stats, pageable),
+             (scion.scion_trace_closest, torch.zeros(4, 8, dtype=torch.float64)),
+             (scion.scion_trace_closest, torch.zeros(8, 4).t())]
+    for fn, t in cases:
+        with pytest.raises(TypeError):
+            fn(None, t)
