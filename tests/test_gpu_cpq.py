@@ -108,3 +108,15 @@ def test_soup_gpu_built_refit_and_counting(sc_mod, oracle_mod):
     with pytest.raises(sc_mod.ScionError) as e:
         query(sc_mod, slab, pts)
     assert e.value.status == 2  # unsupported layout
+
+
+def test_points_in_pinned_host_memory(sc_mod, config1_points):
+    """Query points and results in pinned host memory, read and written by the
+    kernel in place: the same records as from device buffers."""
+    sc, pts, exp = config1_points
+    bvh = sc_mod.scion_build(sc.verts, sc_mod.layout(width=4, box_layout="soa"), sc.indices)
+    h_pts = torch.from_numpy(pts).pin_memory()
+    out = sc_mod.scion_query_closest_point(bvh, h_pts)
+    torch.cuda.synchronize()
+    assert not out.is_cuda and out.is_pinned()
+    same(out.numpy().view(np.uint32).reshape(-1, 4), exp, "pinned points")
