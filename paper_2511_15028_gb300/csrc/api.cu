@@ -1066,6 +1066,11 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   const uint32_t smem_entries = stack_entries(b, p.smem_stack ? p.smem_stack : 16, kQueryClosest);
   TraceKernel k = pick_kernel(b, kQueryClosest, 0);
   if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  const void *k_rays = kernel_view(rays), *k_hits = kernel_view(hits);
+  if (!k_rays || !k_hits) {
+    g_last_error = "ray and result buffers must be device memory or page-locked host memory";
+    return SCION_ERR_INVALID_ARG;
+  }
   void *scratch = nullptr;
   scion_status st = static_scratch(&scratch);
   if (st != SCION_OK) return st;
@@ -1086,8 +1091,8 @@ extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray
   const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
   TraceArgs a;
   bvh_args(b, a);
-  a.rays = reinterpret_cast<const float4 *>(rays);
-  a.out = hits;
+  a.rays = reinterpret_cast<const float4 *>(k_rays);
+  a.out = const_cast<void *>(k_hits);
   a.n = n;
   a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
   a.ordered = order_mode(p.ordered_children);

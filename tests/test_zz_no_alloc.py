@@ -89,6 +89,17 @@ def test_noalloc_rejects_oversize_and_bad_arguments(sc_mod):
                                        ctypes.c_void_p(hits.data_ptr()), ctypes.byref(tiles), s)
     torch.cuda.synchronize()
     assert st == 0 and torch.equal(hits, ref)
+    # pinned host rays and hits are read and written in place; pageable host
+    # memory is rejected before anything is issued
+    h_rays = rays.cpu().pin_memory()
+    h_hits = torch.full((rays.shape[0], 4), -1, dtype=torch.int32).pin_memory()
+    st = L.scion_trace_closest_noalloc(bvh.handle, ctypes.c_void_p(h_rays.data_ptr()), rays.shape[0],
+                                       ctypes.c_void_p(h_hits.data_ptr()), None, s)
+    torch.cuda.synchronize()
+    assert st == 0 and torch.equal(h_hits, ref.cpu())
+    pageable = np.zeros((64, 4), np.int32)
+    assert L.scion_trace_closest_noalloc(bvh.handle, ctypes.c_void_p(rays.data_ptr()), 64,
+                                         ctypes.c_void_p(pageable.ctypes.data), None, s) == 1
     bad = scion.TraceParams(raster_width=128, rays_per_fetch=4)
     assert L.scion_trace_closest_noalloc(bvh.handle, ctypes.c_void_p(rays.data_ptr()), rays.shape[0],
                                          ctypes.c_void_p(hits.data_ptr()), ctypes.byref(bad), s) == 1
