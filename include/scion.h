@@ -284,7 +284,9 @@ scion_status scion_trace_any(scion_bvh bvh, const scion_ray *d_rays, uint64_t n,
  *  d_grad_rays    : device scion_ray-shaped float[n][8] receiving dL/d(o, d)
  *                   (tmin and tmax entries are 0), or NULL.
  * Missed rays (prim = SCION_PRIM_MISS) and errored rays contribute nothing.
- * The per-ray 3x3 solve is done in double precision. */
+ * The per-ray 3x3 solve is done in double precision. Every buffer must be
+ * device memory (the gradients are scattered with device atomics), else
+ * SCION_ERR_INVALID_ARG. */
 scion_status scion_trace_backward(scion_bvh bvh, const scion_ray *d_rays, const scion_hit *d_hits,
                                   const float *d_grad_tuv, uint64_t n, float *d_grad_verts,
                                   scion_ray *d_grad_rays, scion_stream stream);
@@ -312,7 +314,7 @@ scion_status scion_query_closest_point(scion_bvh bvh, const scion_point *d_point
  * (query 0: closest hits into scion_hit[n]; query 1: any-hit flags into
  * uint32[n]; query 2: closest points, d_rays then holding scion_point[n] and
  * d_out scion_closest_point[n]) plus visit counters added into d_counters
- * (device uint64[4]): [0] interior nodes fetched, [1] leaves visited,
+ * (device uint64[4], else SCION_ERR_INVALID_ARG): [0] interior nodes fetched, [1] leaves visited,
  * [2] triangles tested, [3] rays (points) traced. Slower than the plain
  * calls; not for production use. */
 scion_status scion_trace_stats(scion_bvh bvh, const scion_ray *d_rays, uint64_t n, uint32_t query,
@@ -349,8 +351,9 @@ scion_status scion_trace_closest_noalloc(scion_bvh bvh, const scion_ray *d_rays,
  * workload; this lets each scene keep the layout chosen for it while all of
  * them run in one persistent launch.
  *
- * scion_batch_create records scene i = (bvhs[i], d_rays[i] (device
- * scion_ray[n[i]]), d_hits[i] (device scion_hit[n[i]]), per_scene[i] or
+ * scion_batch_create records scene i = (bvhs[i], d_rays[i] (scion_ray[n[i]]),
+ * d_hits[i] (scion_hit[n[i]]), both device or page-locked host memory as for
+ * scion_trace_closest, per_scene[i] or
  * defaults) into a device table (it allocates and uploads; synchronous on
  * `stream`). threads_per_block and smem_stack are taken from per_scene[0].
  * Scenes whose layout is one of the batched node families (width-2 own-box

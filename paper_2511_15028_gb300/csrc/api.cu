@@ -707,6 +707,10 @@ scion_status scion_trace_stats(scion_bvh b, const scion_ray *d_rays, uint64_t n,
                               void *d_out, const scion_trace_params *params, scion_stream stream,
                               uint64_t *d_counters) {
   if (!d_counters || query > 2 || (reinterpret_cast<uintptr_t>(d_counters) & 7u)) return SCION_ERR_INVALID_ARG;
+  if (n > 0 && !is_device_ptr(d_counters)) {  // the kernels add to them with device atomics
+    g_last_error = "d_counters must be device memory";
+    return SCION_ERR_INVALID_ARG;
+  }
   return launch_trace(b, d_rays, n, d_out, params, reinterpret_cast<cudaStream_t>(stream), (int)query,
                       reinterpret_cast<unsigned long long *>(d_counters));
 }
@@ -720,6 +724,12 @@ scion_status scion_trace_backward(scion_bvh b, const scion_ray *d_rays, const sc
       (reinterpret_cast<uintptr_t>(d_grad_rays) & 15u) || (reinterpret_cast<uintptr_t>(d_grad_tuv) & 3u) ||
       (reinterpret_cast<uintptr_t>(d_grad_verts) & 3u))
     return SCION_ERR_INVALID_ARG;
+  // the kernel scatters into the gradients with device atomics: device memory only
+  if (!is_device_ptr(d_rays) || !is_device_ptr(d_hits) || !is_device_ptr(d_grad_tuv) ||
+      !is_device_ptr(d_grad_verts) || (d_grad_rays && !is_device_ptr(d_grad_rays))) {
+    g_last_error = "scion_trace_backward takes device buffers";
+    return SCION_ERR_INVALID_ARG;
+  }
   BackwardArgs a;
   a.rays = reinterpret_cast<const float *>(d_rays);
   a.hits = reinterpret_cast<const uint32_t *>(d_hits);
@@ -779,6 +789,12 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
       return SCION_ERR_INVALID_ARG;
     }
     if (n[i] == 0) continue;
+    const void *k_rays = kernel_view(d_rays[i]), *k_hits = kernel_view(d_hits[i]);
+    if (!k_rays || !k_hits) {
+      g_last_error = "ray and result buffers must be device memory or page-locked host memory";
+      delete bt;
+      return SCION_ERR_INVALID_ARG;
+    }
     const int fam = batched_family(b->own_box ? 1u : 0u, b->desc);
     if (fam < 0) {
       bt->rest_bvh.push_back(b);
@@ -791,8 +807,8 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
     BatchScene sc{};
     TraceArgs &a = sc.a;
     bvh_args(b, a);
-    a.rays = reinterpret_cast<const float4 *>(d_rays[i]);
-    a.out = d_hits[i];
+    a.rays = reinterpret_cast<const float4 *>(k_rays);
+    a.out = const_cast<void *>(k_hits);
     a.n = n[i];
     a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
     a.ordered = order_mode(p.ordered_children);

@@ -2,6 +2,8 @@
 and rays. The GPU backward (FP32 atomic scatter) is checked against the FP64
 CPU reference gradient and against central differences, and the autograd
 wrapper returns the same numbers."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -101,3 +103,25 @@ def test_autograd_function_and_accumulation(setup):
                                         torch.from_numpy(g).cuda(), grad_verts=verts.grad.clone(),
                                         want_ray_grads=False)
     assert np.all(np.abs(gv2.cpu().numpy() - 2 * gvv) <= 2e-5 * S + 2e-6)
+
+
+def test_backward_and_counters_take_device_buffers_only(setup):
+    """Gradients and visit counters are added with device atomics: host
+    buffers are rejected before any launch."""
+    scion = setup[0]
+    sc = scenes.config1_scene()
+    bvh = scion.scion_build(sc.verts, scion.layout(), sc.indices)
+    rays = torch.from_numpy(scenes.config1_rays()[:64]).cuda()
+    hits = scion.scion_trace_closest(bvh, rays)
+    L = scion.lib()
+    host_grad = np.zeros((sc.verts.shape[0], 3), np.float32)
+    g_tuv = torch.zeros((64, 3), device="cuda")
+    st = L.scion_trace_backward(bvh.handle, ctypes.c_void_p(rays.data_ptr()), ctypes.c_void_p(hits.data_ptr()),
+                                ctypes.c_void_p(g_tuv.data_ptr()), 64, ctypes.c_void_p(host_grad.ctypes.data),
+                                None, None)
+    assert st == 1
+    out = torch.empty((64, 4), dtype=torch.int32, device="cuda")
+    host_cnt = np.zeros(4, np.uint64)
+    st = L.scion_trace_stats(bvh.handle, ctypes.c_void_p(rays.data_ptr()), 64, 0, ctypes.c_void_p(out.data_ptr()),
+                             None, None, ctypes.c_void_p(host_cnt.ctypes.data))
+    assert st == 1
