@@ -75,6 +75,11 @@ void scion_debug_host_destroy(scion_host_bvh hb);
 uint32_t scion_debug_f16_round(float x, int dir);
 float scion_debug_f16_decode(uint32_t h);
 
+/* Warp-batch slots of a launch over n rays with the traversal parameter
+ * raster_width = w (0: n; else 32 per 8 x 4 pixel tile, up to the last tile
+ * that holds a ray): the loop bound the trace kernels get. Host only. */
+uint64_t scion_debug_raster_slots(uint64_t n, uint32_t raster_width);
+
 /* Message of the last host-side error (static storage, not thread-safe). */
 const char *scion_last_error(void);
 

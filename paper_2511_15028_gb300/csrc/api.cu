@@ -997,6 +997,14 @@ scion_status scion_debug_host_decode(scion_host_bvh h, uint32_t *kind, uint32_t 
   return SCION_OK;
 }
 
+uint64_t scion_debug_raster_slots(uint64_t n, uint32_t raster_width) {
+  if (n == 0) return 0;
+  TraceArgs a{};
+  a.n = n;
+  set_raster(a, raster_width);
+  return a.n_work;
+}
+
 scion_status scion_debug_host_raw(scion_host_bvh h, void *nodes, uint64_t nodes_cap, void *nodes2,
                                   uint64_t nodes2_cap, float *frame) {
   if (!h || !frame) return SCION_ERR_INVALID_ARG;

@@ -161,6 +161,8 @@ def lib():
         L.scion_debug_host_destroy.restype = None
         L.scion_debug_f16_round.argtypes = [ctypes.c_float, I]
         L.scion_debug_f16_round.restype = U32
+        L.scion_debug_raster_slots.argtypes = [U64, U32]
+        L.scion_debug_raster_slots.restype = U64
         L.scion_debug_f16_decode.argtypes = [U32]
         L.scion_debug_f16_decode.restype = ctypes.c_float
         for name in ("scion_build", "scion_build_gpu", "scion_bvh_build_times", "scion_refit",

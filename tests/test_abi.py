@@ -86,3 +86,28 @@ def test_python_binding_rejects_unreachable_buffers_without_gpu():
     for fn, t in cases:
         with pytest.raises(TypeError):
             fn(None, t)
+
+
+def test_camera_ray_tiles_cover_every_ray_once(libscion):
+    """Host logic of raster_width: the slot count the kernels loop over
+    (scion_debug_raster_slots) ends at the last 8x4 tile holding a ray, and the
+    kernels' slot -> pixel mapping (slot s: tile s // 32, lane s % 32 at column
+    8 (t mod tiles_x) + lane mod 8, row 4 (t div tiles_x) + lane div 8) reaches
+    every ray exactly once, for ragged widths and partial last rows."""
+    libscion.scion_debug_raster_slots.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+    libscion.scion_debug_raster_slots.restype = ctypes.c_uint64
+    for n in list(range(1, 40)) + [100, 127, 128, 129, 1000, 4096]:
+        assert libscion.scion_debug_raster_slots(n, 0) == n
+        for w in (1, 2, 3, 7, 8, 9, 16, 17, 33, 100, 128, 1 << 20):
+            slots = libscion.scion_debug_raster_slots(n, w)
+            tiles_x = (w + 7) // 8
+            # the last tile holding a ray, from the rays' side
+            last = max((i // w // 4) * tiles_x + (i % w) // 8 for i in range(n))
+            assert slots == 32 * (last + 1), (n, w, slots)
+            s = np.arange(slots)
+            t, lane = s // 32, s % 32
+            px = (t % tiles_x) * 8 + (lane & 7)
+            py = (t // tiles_x) * 4 + (lane >> 3)
+            rid = py * w + px
+            hit = rid[(px < w) & (rid < n)]
+            assert np.array_equal(np.sort(hit), np.arange(n)), (n, w)
