@@ -9,12 +9,14 @@
 // 256-bit non-coherent loads (node strides are multiples of 32 bytes).
 //
 // Execution model: a persistent grid (a few CTAs per SM); each warp takes 32
-// rays at a time from a global counter with one atomicAdd; each lane traces
-// one ray with a per-thread stack whose first entries live in shared memory
-// (strided by blockDim, conflict-free) and whose tail spills to local memory.
-// The current entry is always in registers. (A variant that refilled idle
-// lanes mid-warp needed 74 instead of 64 registers, lost a quarter of the
-// occupancy and gained no SIMT efficiency; it was measured and dropped.)
+// rays at a time from a global counter with one atomicAdd (or an 8x4 pixel
+// tile of a row-major image of camera rays), or refills its idle lanes from
+// its CTA's share once enough of them are idle (body_refill); each lane
+// traces one ray with a per-thread stack whose first entries live in shared
+// memory (strided by blockDim, conflict-free) and whose tail spills to local
+// memory, or, where a kernel has the register for it, whose shared part is a
+// ring of the most recent entries (StackT). The current entry is always in
+// registers.
 //
 // Arithmetic: the box test only has to be conservative; the triangle test is
 // pinned bit for bit (see tri_test). Translation units are compiled with
