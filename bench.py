@@ -68,33 +68,57 @@ def tri_load_bytes(desc, indexed: bool) -> int:
     return 4 + (12 if indexed else 0) + 48
 
 
-# ------------------------------------------------------------------ profiled DRAM traffic
+# ------------------------------------------------------------------ profiled traffic
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_kernel_traffic.txt")
+KERNEL_SOURCES = ("trace.cuh", "trace_inst.cu", "layout.h", "kernels.h")
+
+
+def _strip_comments(src: str) -> str:
+    """C/C++ source without comments and with whitespace collapsed: edits of
+    comments or layout leave the hash (and so the recorded counters) valid."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_sources_hash() -> str:
+    """Hash of the traversal kernel's code (comments stripped) and of the
+    nvcc flags it is built with."""
     import hashlib
+
+    from paper_2511_15028_gb300 import build as native_build
     h = hashlib.sha256()
-    for f in ("trace.cuh", "trace_inst.cu", "layout.h", "kernels.h"):
-        h.update(open(os.path.join(ROOT, "paper_2511_15028_gb300", "csrc", f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(_strip_comments(open(os.path.join(ROOT, "paper_2511_15028_gb300", "csrc", f)).read()).encode())
+    h.update(" ".join(native_build.ARCH + native_build.NVCC_FLAGS[:-1]).encode())
     return h.hexdigest()
 
 
-def profiled_traffic(query: str):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel sources changed since that capture."""
-    p = os.path.join(ROOT, "profiles", "trace_kernel_coherent_bvh4_full.md")
-    if not os.path.exists(p):
+def profiled_traffic(workload: str, layout: str, query: str):
+    """(DRAM bytes, L2 bytes) per launch of the traversal kernel on this
+    workload, layout and query, from the committed ncu summary
+    profiles/trace_kernel_traffic.txt; None when it holds no such capture or
+    the kernel's code has changed since it was taken."""
+    if not os.path.exists(TRAFFIC_FILE):
         return None
-    txt = open(p).read()
-    vals, sha = {}, None
-    for line in txt.splitlines():
-        if line.startswith("traffic_dram_bytes_per_launch:"):
-            for kv in line.split(":", 1)[1].split():
-                k, v = kv.split("=")
-                vals[k] = int(v)
-        if line.startswith("kernel_sources_sha256:"):
-            sha = line.split(":", 1)[1].strip()
-    if sha != kernel_sources_hash():
+    sha, rows = None, {}
+    for line in open(TRAFFIC_FILE):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "kernel_sources_sha256":
+            sha = f[1]
+        elif len(f) >= 4 and f[0] in ("coherent", "incoherent"):
+            kv = dict(x.split("=", 1) for x in f[3:] if "=" in x)
+            rows[(f[0], f[1], f[2])] = kv
+    if sha is None or sha != kernel_sources_hash():
         return None
-    return vals.get(query)
+    kv = rows.get((workload, layout, query))
+    if kv is None:
+        return None
+    return {"dram_bytes": int(kv["dram_bytes"]), "l2_bytes": int(kv["l2_bytes"]),
+            "fetch": kv.get("fetch"), "source": os.path.relpath(TRAFFIC_FILE, ROOT)}
 
 
 # ------------------------------------------------------------------ clocks
@@ -160,6 +184,40 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# ------------------------------------------------------------------ L2 read peak
+def measure_l2_peak(scion, torch, sizes_mib=(16, 32, 48, 64), target_ms=1.0, trials=7):
+    """L2 read bandwidth of this GPU, measured live: the library's read probe
+    (16-byte loads that bypass L1, every SM) streams an L2-resident buffer many
+    times in one launch, timed with CUDA events; best of `trials` launches per
+    buffer size. The roofline peak is the largest rate over the sizes."""
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = {}
+    for mib in sizes_mib:
+        buf = torch.randint(0, 1 << 30, ((mib << 20) // 4,), dtype=torch.int32, device="cuda")
+        nbytes = buf.numel() * 4
+        scion.scion_debug_read_bandwidth(buf, 1, sink)  # bring it into L2
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        scion.scion_debug_read_bandwidth(buf, 8, sink)
+        b.record()
+        b.synchronize()
+        reps = max(8, int(8 * target_ms / max(a.elapsed_time(b), 1e-3)))
+        best = 0.0
+        for _ in range(trials):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            scion.scion_debug_read_bandwidth(buf, reps, sink)
+            b.record()
+            b.synchronize()
+            best = max(best, nbytes * reps / (a.elapsed_time(b) / 1e3) / 1e9)
+        out[f"{mib}MiB"] = round(best, 1)
+        del buf
+    return {"peak_gbs": max(out.values()), "by_size_gbs": out,
+            "how": "ld.global.cg 16-byte loads over an L2-resident buffer, every SM, one launch of many passes, "
+                   f"best of {trials} launches per size (CUDA events)"}
+
+
 # ------------------------------------------------------------------ workload
 def make_workload(scion, torch, dev, primary_desc):
     from paper_2511_15028_gb300 import scenes
@@ -179,15 +237,23 @@ def flush_l2(buf):
 
 # Traversal parameters tried per layout and kind of ray (fetch mode x child
 # order); any-hit ignores the child order.
-FETCH_MODES = {"warp_batch": {}, "refill1": {"rays_per_fetch": 1}, "refill8": {"rays_per_fetch": 8},
-               "refill16": {"rays_per_fetch": 16},
+_BASE_MODES = {"warp_batch": {}, "refill1": {"rays_per_fetch": 1}, "refill4": {"rays_per_fetch": 4},
+               "refill8": {"rays_per_fetch": 8}, "refill16": {"rays_per_fetch": 16},
                "warp_batch/nearest_first": {"ordered_children": 3},
                "refill1/nearest_first": {"rays_per_fetch": 1, "ordered_children": 3},
                "refill8/nearest_first": {"rays_per_fetch": 8, "ordered_children": 3}}
+# each mode also with the newest 4 stack entries in registers (and 2 for the
+# two most used modes)
+FETCH_MODES = dict(_BASE_MODES)
+FETCH_MODES.update({f"{k}/reg4": {**v, "reg_stack": 4} for k, v in _BASE_MODES.items()})
+FETCH_MODES.update({f"{k}/reg2": {**_BASE_MODES[k], "reg_stack": 2} for k in ("warp_batch", "refill8")})
 # Primary rays are a row-major 1920-wide image: warps can take 8x4 pixel tiles.
 PRIMARY_RASTER = 1920
 RASTER_MODES = {"tiles": {"raster_width": PRIMARY_RASTER},
-                "tiles/nearest_first": {"raster_width": PRIMARY_RASTER, "ordered_children": 3}}
+                "tiles/nearest_first": {"raster_width": PRIMARY_RASTER, "ordered_children": 3},
+                "tiles/reg4": {"raster_width": PRIMARY_RASTER, "reg_stack": 4},
+                "tiles/nearest_first/reg4": {"raster_width": PRIMARY_RASTER, "ordered_children": 3,
+                                             "reg_stack": 4}}
 
 
 def mode_params(name):
@@ -448,8 +514,19 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
         out[name] = res
         scion.scion_destroy(bvh)
     best = max(out, key=lambda k: out[k]["closest"]["mrays_s"])
+    best_any = max(out, key=lambda k: out[k]["any"]["mrays_s"])
+    roof = {}
+    for q, name in (("closest", best), ("any", best_any)):
+        prof = profiled_traffic("incoherent", name, q)
+        rq = out[name][q]
+        roof[q] = {"bound": "hbm", "layout": name, "achieved": round(rq["alg_gbs"], 1), "peak": hbm_peak,
+                   "unit": "GB/s", "frac": round(rq["roofline_frac_of_measured_hbm"], 4),
+                   "traffic": prof["dram_bytes"] if prof else None,
+                   "l2_traffic": prof["l2_bytes"] if prof else None,
+                   "traffic_source": prof["source"] if prof else None,
+                   "note": "the BVH is far larger than L2: the roof is the measured HBM copy bandwidth"}
     return {"tris": sc.n_tris, "rays": n, "gen_s": round(gen_s, 1), "build_layouts_s": round(build_s, 1),
-            "layouts": out, "best_closest": best,
+            "roofline": roof, "layouts": out, "best_closest": best, "best_any": best_any,
             "pareto_closest": pareto({k: (v["bvh_mb"], v["closest"]["mrays_s"]) for k, v in out.items()}),
             "pareto_any": pareto({k: (v["bvh_mb"], v["any"]["mrays_s"]) for k, v in out.items()})}
 
@@ -651,7 +728,14 @@ def bench_batched(scion, torch, steps, warmup, flush_buf, seed=1004):
             ts.append(a.elapsed_time(b))
         return trimmed_mean(ts)
 
+    # the same 64 plain launches captured into one CUDA graph: no host issue
+    # cost in the timed region, so the batched launch's gain over it is the
+    # traversal's and the load balance's, not the host's
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp, stream=stream):
+        plain()
     t_batch = timed(g.replay)
+    t_plain_graph = timed(gp.replay)
     t_plain = timed(plain)
     t_dflt = timed(plain_default)
     identical = all(torch.equal(a, b) for a, b in zip(batch.hits, plain_out))
@@ -661,27 +745,26 @@ def bench_batched(scion, torch, steps, warmup, flush_buf, seed=1004):
     for c in chosen:
         k = c.name + ("/slot" if c.params else "/ordered")
         picks[k] = picks.get(k, 0) + 1
+    info = batch.info()
     return {"scenes": len(wl), "tris": int(n_tris), "rays": int(n_rays),
-            "batched_graph_ms": t_batch, "plain_same_layouts_ms": t_plain, "plain_default_layout_ms": t_dflt,
+            "batched_graph_ms": t_batch, "plain_graph_ms": t_plain_graph, "plain_host_ms": t_plain,
+            "plain_default_layout_ms": t_dflt,
             "mrays_s_batched": n_rays / (t_batch / 1e3) / 1e6,
-            "speedup_vs_plain": t_plain / t_batch, "speedup_vs_default": t_dflt / t_batch,
+            "speedup_vs_plain_graph": t_plain_graph / t_batch, "speedup_vs_plain_host": t_plain / t_batch,
+            "speedup_vs_default": t_dflt / t_batch, "batched_scenes": info["batched_scenes"],
+            "plain_scenes": info["plain_scenes"],
             "hits_identical": bool(identical), "autotune_picks": picks,
             "gen_s": round(gen_s, 1), "build_and_tune_s": round(tune_s, 1)}
 
 
 # ------------------------------------------------------------------ differentiation (config 5)
-def bench_backward(scion, torch, steps, warmup):
-    """Config-1 scene and rays, L = sum w t + a u + b v: forward alone against
-    forward + backward (dL/dvertex via FP32 atomics, dL/dray)."""
-    from paper_2511_15028_gb300 import scenes
-    sc = scenes.config1_scene()
-    rays = torch.from_numpy(scenes.config1_rays()).cuda()
-    w, a, b = scenes.config5_weights(rays.shape[0])
-    g = torch.from_numpy(np.stack([w, a, b], -1)).cuda()
-    bvh = scion.scion_build(sc.verts, scion.layout(width=4, box_layout="soa", prim_ref="direct"), sc.indices)
-    hits = torch.empty((rays.shape[0], 4), dtype=torch.int32, device="cuda")
-    gv = torch.zeros((sc.verts.shape[0], 3), dtype=torch.float32, device="cuda")
-    gr = torch.empty((rays.shape[0], 8), dtype=torch.float32, device="cuda")
+def _fwd_bwd_times(scion, torch, bvh, rays, g, n_verts, steps, warmup, reps, flush_buf=None):
+    """Trimmed-mean ms of the forward trace alone and of forward + backward
+    (dL/dvertex via FP32 atomics into a zeroed buffer, dL/dray)."""
+    n = rays.shape[0]
+    hits = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    gv = torch.zeros((n_verts, 3), dtype=torch.float32, device="cuda")
+    gr = torch.empty((n, 8), dtype=torch.float32, device="cuda")
 
     def fwd():
         scion.scion_trace_closest(bvh, rays, hits)
@@ -691,12 +774,14 @@ def bench_backward(scion, torch, steps, warmup):
         gv.zero_()
         scion.scion_trace_backward(bvh, rays, hits, g, grad_verts=gv, grad_rays=gr)
 
-    def timed(fn, reps=50):
+    def timed(fn):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         ts = []
         for _ in range(steps):
+            if flush_buf is not None:
+                flush_l2(flush_buf)
             a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a_.record()
             for _ in range(reps):
@@ -706,13 +791,70 @@ def bench_backward(scion, torch, steps, warmup):
             ts.append(a_.elapsed_time(b_) / reps)
         return trimmed_mean(ts)
 
-    tf, tfb = timed(fwd), timed(fwd_bwd)
+    return timed(fwd), timed(fwd_bwd)
+
+
+def bench_backward(scion, torch, steps, warmup, flush_buf=None):
+    """Config-1 scene and rays, L = sum w t + a u + b v: forward alone against
+    forward + backward; and the same at the coherent scene's scale (1920 x 1080
+    primary rays on 1,373,138 triangles), where launch overhead no longer hides
+    the backward kernel."""
+    from paper_2511_15028_gb300 import scenes
+    lay = scion.layout(width=4, box_layout="soa", prim_ref="direct")
+    out = {}
+    sc = scenes.config1_scene()
+    rays = torch.from_numpy(scenes.config1_rays()).cuda()
+    w, a, b = scenes.config5_weights(rays.shape[0])
+    g = torch.from_numpy(np.stack([w, a, b], -1)).cuda()
+    bvh = scion.scion_build(sc.verts, lay, sc.indices)
+    tf, tfb = _fwd_bwd_times(scion, torch, bvh, rays, g, sc.verts.shape[0], steps, warmup, 50)
     n = rays.shape[0]
-    return {"rays": n, "fwd_ms": tf, "fwd_bwd_ms": tfb, "mrays_s_fwd": n / (tf / 1e3) / 1e6,
-            "mrays_s_fwd_bwd": n / (tfb / 1e3) / 1e6, "fwd_bwd_over_fwd": tfb / tf}
+    out["c5_16384_rays"] = {"rays": n, "fwd_ms": tf, "fwd_bwd_ms": tfb, "mrays_s_fwd": n / (tf / 1e3) / 1e6,
+                            "mrays_s_fwd_bwd": n / (tfb / 1e3) / 1e6, "fwd_bwd_over_fwd": tfb / tf,
+                            "timing": "50 back-to-back calls per timed step (launch-bound size)"}
+    sc2 = scenes.config2_scene()
+    rays2 = torch.from_numpy(scenes.config2_primary()).cuda()
+    w, a, b = scenes.config5_weights(rays2.shape[0])
+    g2 = torch.from_numpy(np.stack([w, a, b], -1)).cuda()
+    bvh2 = scion.scion_build(sc2.verts, lay, sc2.indices)
+    tf, tfb = _fwd_bwd_times(scion, torch, bvh2, rays2, g2, sc2.verts.shape[0], steps, warmup, 1, flush_buf)
+    n = rays2.shape[0]
+    out["coherent_primary_2073600_rays"] = {
+        "rays": n, "tris": sc2.n_tris, "fwd_ms": tf, "fwd_bwd_ms": tfb, "bwd_ms": tfb - tf,
+        "mrays_s_fwd": n / (tf / 1e3) / 1e6, "mrays_s_fwd_bwd": n / (tfb / 1e3) / 1e6,
+        "fwd_bwd_over_fwd": tfb / tf, "timing": "one call per timed step, L2 flushed between steps"}
+    return out
 
 
 # ------------------------------------------------------------------ main
+def _peaks():
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(pk)) if os.path.exists(pk) else {}
+    hbm = peaks.get("hbm_gbs")
+    return (hbm, "of measured") if hbm else (6800.0, "of fallback")
+
+
+def emit(rank, obj):
+    """One JSON line on stdout (rank 0 only)."""
+    if rank == 0:
+        print(json.dumps(obj), flush=True)
+
+
+def run_section(rank, name, fn, *a, **kw):
+    """Run one measurement section and print it as its own JSON line; a
+    failing section prints its error and the run goes on."""
+    try:
+        res = fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 - reported in the section's line
+        emit(rank, {"section": name, "error": f"{type(e).__name__}: {e}"})
+        return None
+    emit(rank, {"section": name, **res})
+    return res
+
+
+SECTIONS = ("incoherent", "batched", "backward", "build", "cpq", "l2")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -724,10 +866,10 @@ def main():
     ap.add_argument("--fetch", default=None,
                     help="primary,bounce,shadow fetch modes (names of FETCH_MODES / RASTER_MODES); skips the "
                          "per-layout trials, e.g. to profile exactly the modes a plain run chose")
-    ap.add_argument("--no-extra", action="store_true", help="skip the incoherent, batched and backward measurements")
-    ap.add_argument("--section", default="all", choices=["all", "incoherent", "build", "cpq"],
-                    help="incoherent: only the 2^23-triangle section (for profiling); "
-                         "build: only the host/GPU construction section")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the incoherent, batched, backward, build and closest point sections")
+    ap.add_argument("--section", default="all", choices=("all",) + SECTIONS,
+                    help="run only one section (e.g. for profiling) and print its line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -753,27 +895,18 @@ def main():
     native_build.build()
     from paper_2511_15028_gb300 import scion
 
-    if args.section == "cpq":
-        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-        peak = json.load(open(pk)).get("hbm_gbs", 6800.0) if os.path.exists(pk) else 6800.0
-        res = bench_cpq(scion, torch, args.steps, args.warmup, peak)
-        if rank == 0:
-            print(json.dumps({"section": "cpq", "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
-        return
-
-    if args.section == "build":
-        res = bench_build(scion, torch, args.steps, args.warmup)
-        if rank == 0:
-            print(json.dumps({"section": "build", "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
-        return
-
-    if args.section == "incoherent":
-        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-        peak = json.load(open(pk)).get("hbm_gbs", 6800.0) if os.path.exists(pk) else 6800.0
+    hbm_peak, peak_src = _peaks()
+    if args.section != "all":
         only = None if args.layouts == "all" else args.layouts.split(",")
-        res = bench_incoherent(scion, torch, args.steps, args.warmup, peak, only)
-        if rank == 0:
-            print(json.dumps({"section": "incoherent", "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        fns = {"incoherent": lambda: bench_incoherent(scion, torch, args.steps, args.warmup, hbm_peak, only),
+               "batched": lambda: bench_batched(scion, torch, args.steps, args.warmup, flush),
+               "backward": lambda: bench_backward(scion, torch, args.steps, args.warmup, flush),
+               "build": lambda: bench_build(scion, torch, args.steps, args.warmup),
+               "cpq": lambda: bench_cpq(scion, torch, args.steps, args.warmup, hbm_peak),
+               "l2": lambda: measure_l2_peak(scion, torch)}
+        res = fns[args.section]()
+        emit(rank, {"section": args.section, "steps": args.steps, "warmup": args.warmup, **res})
         return
 
     layouts = scion.sweep_layouts(extended=True)
@@ -790,13 +923,10 @@ def main():
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     props = torch.cuda.get_device_properties(dev)
     bus = getattr(props, "pci_bus_id", None)
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = json.load(open(pk))
-    hbm_peak = peaks.get("hbm_gbs")
-    peak_src = "of measured" if hbm_peak else "of fallback"
-    hbm_peak = hbm_peak or 6800.0
+
+    # the roof of an L2-resident traversal: this GPU's L2 read bandwidth
+    l2 = measure_l2_peak(scion, torch)
+    emit(rank, {"section": "l2_peak", **l2})
 
     results = {}
     sampler = ClockSampler(bus) if rank == 0 else None
@@ -830,13 +960,14 @@ def main():
             "mrays_s": world * sum(n_rays) / (ms / 1e3) / 1e6,
             "ms_per_step": ms,
             "per_query_ms": {"primary": per_ms[0], "bounce": per_ms[1], "shadow": per_ms[2]},
-            "per_query_mrays_s": {q: n_rays[i] / (per_ms[i] / 1e3) / 1e6
-                                  for i, q in enumerate(("primary", "bounce", "shadow"))},
             "bvh_mb": (info["node_bytes"] + info["prim_bytes"]) / 1e6,
             "node_mb": info["node_bytes"] / 1e6, "n_nodes": info["n_nodes"], "depth": info["depth"],
-            "bytes_per_ray": {q: alg[i] / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
-            "nodes_per_ray": {q: float(cnt[i][0]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
-            "tris_per_ray": {q: float(cnt[i][2]) / max(1, n_rays[i]) for i, q in enumerate(("primary", "bounce", "shadow"))},
+            "bytes_per_ray": {q: round(alg[i] / max(1, n_rays[i]), 1)
+                              for i, q in enumerate(("primary", "bounce", "shadow"))},
+            "nodes_per_ray": {q: round(float(cnt[i][0]) / max(1, n_rays[i]), 2)
+                              for i, q in enumerate(("primary", "bounce", "shadow"))},
+            "tris_per_ray": {q: round(float(cnt[i][2]) / max(1, n_rays[i]), 2)
+                             for i, q in enumerate(("primary", "bounce", "shadow"))},
             "alg_bytes": alg, "device_status": st_status,
             "fetch_mode": {"primary": modes[0], "bounce": modes[1], "shadow": modes[2]},
             "fetch_trials_ms": dict(zip(("primary", "bounce", "shadow"), trials)),
@@ -850,15 +981,24 @@ def main():
     # primary and bounce launches take most of the step); per-launch averages
     tq = r["per_query_ms"]["primary"] + r["per_query_ms"]["bounce"]
     achieved = (r["alg_bytes"][0] + r["alg_bytes"][1]) / (tq / 1e3) / 1e9
-    traffic = profiled_traffic("closest") if best == "bvh4_soa_f32_direct" else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic,
+    prof = profiled_traffic("coherent", best, "closest")
+    l2_peak = l2["peak_gbs"]
+    roofline = {"bound": "l2", "achieved": round(achieved, 1), "peak": l2_peak, "unit": "GB/s",
+                "frac": round(achieved / l2_peak, 4),
+                "traffic": prof["dram_bytes"] if prof else None,
+                "l2_traffic": prof["l2_bytes"] if prof else None,
+                "traffic_source": prof["source"] if prof else None,
                 "kernel": f"trace_kernel closest hit ({best}; primary + bounce launches)",
-                "peak_source": peak_src,
+                "peak_source": "measured live in this run: L2 read bandwidth (section l2_peak)",
+                "frac_of_measured_hbm": round(achieved / hbm_peak, 4), "hbm_peak": hbm_peak,
+                "hbm_peak_source": peak_src,
                 "note": "algorithmic bytes = rays x 48 + nodes visited x node bytes + triangles tested x "
-                        "triangle bytes (counting kernel); this BVH fits in L2, so DRAM traffic is far lower; "
-                        "the bounce launch shares the GPU with the concurrent shadow launch, so its duration "
-                        "and this figure are conservative"}
+                        "triangle bytes (counting kernel) over the launches' CUDA-event durations; the BVH "
+                        "fits in L2, so the roof is the L2 read bandwidth and DRAM traffic (traffic) is small"}
+    emit(rank, {"section": "coherent_layouts", "workload": WORKLOAD, "best": best,
+                "pareto": pareto({k: (v["bvh_mb"], v["mrays_s"]) for k, v in results.items()}),
+                "layouts": {k: {kk: vv for kk, vv in v.items() if kk not in ("alg_bytes", "_bvh")}
+                            for k, v in results.items()}})
     # end to end through host buffers, best layout
     fm = r["fetch_mode"]
     e2e_t, bi, bo = e2e_layout(scion, torch, r["_bvh"], (prim, bounce, shadow), args.steps, args.warmup, flush_buf,
@@ -876,40 +1016,42 @@ def main():
                        "pinned host memory over NVLink-C2C (scion.HostTracer(zero_copy=True))",
            "staged_copies": {"value": world * sum(n_rays) / (staged_ms / 1e3) / 1e6, "ms_per_step": staged_ms,
                              "how": "cudaMemcpyAsync of 1M-ray chunks on three streams overlapping the traces"}}
+    headline_bvh = r["_bvh"]
     for v in results.values():
         v.pop("_bvh", None)
-    extra = {"pareto_coherent": pareto({k: (v["bvh_mb"], v["mrays_s"]) for k, v in results.items()})}
+    del headline_bvh
     if not args.no_extra:
-        extra["incoherent"] = bench_incoherent(scion, torch, args.steps, args.warmup, hbm_peak)
-        extra["batched"] = bench_batched(scion, torch, args.steps, args.warmup, flush_buf)
-        extra["backward"] = bench_backward(scion, torch, args.steps, args.warmup)
-        extra["build"] = bench_build(scion, torch, args.steps, args.warmup)
-        extra["closest_point"] = bench_cpq(scion, torch, args.steps, args.warmup, hbm_peak)
+        run_section(rank, "incoherent", bench_incoherent, scion, torch, args.steps, args.warmup, hbm_peak)
+        run_section(rank, "batched", bench_batched, scion, torch, args.steps, args.warmup, flush_buf)
+        run_section(rank, "backward", bench_backward, scion, torch, args.steps, args.warmup, flush_buf)
+        run_section(rank, "build", bench_build, scion, torch, args.steps, args.warmup)
+        run_section(rank, "closest_point", bench_cpq, scion, torch, args.steps, args.warmup, hbm_peak)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         cpu = cpu_baseline()
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": r["mrays_s"], "unit": "Mrays/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "layout": best, "rays_per_step": int(sum(n_rays)),
-                       "rays": {"primary": n_rays[0], "bounce": n_rays[1], "shadow": n_rays[2]},
-                       "l2": "flushed (512 MiB write) between timed steps",
-                       "timing": "primary closest hit, then bounce closest hit and shadow any hit concurrently "
-                                 "on two streams (both come from the primary hits); CUDA events per launch on its "
-                                 "stream and around the step on the main stream; trimmed mean of K steps",
-                       "parallelism": f"replicas x{world}"},
-            "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
-            "bvh_mb": r["bvh_mb"],
-            "layouts": {k: {kk: vv for kk, vv in v.items() if kk not in ("alg_bytes",)} for k, v in results.items()},
-            **extra,
-        }
-        print(json.dumps(line), flush=True)
+    line = {
+        "metric": METRIC, "value": r["mrays_s"], "unit": "Mrays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "layout": best, "rays_per_step": int(sum(n_rays)),
+                   "rays": {"primary": n_rays[0], "bounce": n_rays[1], "shadow": n_rays[2]},
+                   "fetch_modes": r["fetch_mode"],
+                   "l2": "flushed (512 MiB write) between timed steps",
+                   "timing": "primary closest hit, then bounce closest hit and shadow any hit concurrently "
+                             "on two streams (both come from the primary hits); CUDA events around the step "
+                             "on the main stream; trimmed mean of K steps",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "bvh_mb": round(r["bvh_mb"], 2),
+        "per_query_ms": {k: round(v, 4) for k, v in r["per_query_ms"].items()},
+        "sections": "earlier JSON lines: l2_peak, coherent_layouts (every layout, Pareto front)"
+                    + ("" if args.no_extra else ", incoherent, batched, backward, build, closest_point"),
+    }
+    emit(rank, line)
     if dist is not None:
         dist.destroy_process_group()
 

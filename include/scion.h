@@ -17,7 +17,12 @@
  *    the host. Errors found on the device (stack overflow, step limit) are
  *    recorded in the BVH's device status word and the affected ray's hit gets
  *    prim = SCION_PRIM_ERROR; scion_get_status reads and clears that word.
- *  - Device pointers are CUDA device addresses on the current device.
+ *  - Device pointers are CUDA device addresses on the current device. A BVH
+ *    is used on the device it was built on: a call on it while another
+ *    device is current, or with device memory of another GPU, returns
+ *    SCION_ERR_INVALID_ARG before anything is issued.
+ *  - scion_last_error() holds the message of the last failing call of the
+ *    calling host thread.
  *  - Rays and hits are caller-owned. The BVH owns its own device buffers.
  *  - One BVH may be traced concurrently from up to 64 distinct streams: each
  *    stream gets its own work counter in the BVH (calls on one stream run in
@@ -128,7 +133,15 @@ typedef struct {
 /* Traversal parameters; NULL or 0 fields = defaults.
  *  threads_per_block : CTA size (multiple of 32, <= 1024; default 256).
  *  ctas_per_sm       : persistent CTAs per SM (default: from occupancy).
- *  reg_stack         : reserved (0).
+ *  reg_stack         : entries of the traversal stack kept in registers
+ *                      (0, 2 or 4; default 0): the newest entries stay in
+ *                      registers and older ones move to the shared-memory
+ *                      part (then local memory), which saves a shared-memory
+ *                      store and load per entry that is popped while still
+ *                      in registers. The paper's traversal uses a 64-entry
+ *                      stack (Section 9.2). Results are identical. Other
+ *                      values, or a non-zero value for closest point
+ *                      queries: SCION_ERR_INVALID_ARG.
  *  smem_stack        : shared-memory stack entries per thread (default 16,
  *                      at most 64; own-box bvh2 layouts other than the shared
  *                      slab round it down to a power of two).

@@ -8,8 +8,9 @@
  * decode call reads every packed node back into its logical view (child
  * kind, child node or leaf range, conservative box).
  *
- * All pointers here are host memory owned by the caller. None of these calls
- * touches a GPU.
+ * All pointers here are host memory owned by the caller, and none of these
+ * calls touches a GPU, except scion_debug_read_bandwidth (a measurement
+ * probe, device memory).
  */
 #ifndef SCION_DEBUG_H
 #define SCION_DEBUG_H
@@ -80,7 +81,21 @@ float scion_debug_f16_decode(uint32_t h);
  * that holds a ray): the loop bound the trace kernels get. Host only. */
 uint64_t scion_debug_raster_slots(uint64_t n, uint32_t raster_width);
 
-/* Message of the last host-side error (static storage, not thread-safe). */
+/* Measurement probe for the roofline of traversals whose BVH fits in L2 (the
+ * bandwidth bound of Section 9.2's finding that compact layouts win by moving
+ * fewer bytes): one launch that reads the device buffer d_buf (bytes, a
+ * multiple of 16, 16-byte aligned) `reps` times with 16-byte loads that
+ * bypass L1 (ld.global.cg), from every SM, asynchronously on `stream`. A
+ * buffer well below the L2 size stays in L2, so bytes * reps / (launch time)
+ * is the L2 read bandwidth; the caller times the launch (CUDA events on
+ * `stream`). d_sink: device uint32 that the kernel may write (it keeps the
+ * loads from being optimised away; its value means nothing). Both buffers
+ * must be device memory of the current device, else SCION_ERR_INVALID_ARG. */
+scion_status scion_debug_read_bandwidth(const void *d_buf, uint64_t bytes, uint32_t reps, uint32_t *d_sink,
+                                        scion_stream stream);
+
+/* Message of the last failing call on the calling host thread (kept per
+ * thread; valid until that thread's next failing call). */
 const char *scion_last_error(void);
 
 #ifdef __cplusplus

@@ -87,9 +87,12 @@ static int tri_finite(const float *p) {
  *   det = (U + V) + W, miss if zero;
  *   T = fma(W, Sz*C[kz], fma(V, Sz*B[kz], U*(Sz*A[kz])));
  *   t = T/det, u = V/det (weight of p1), v = W/det (weight of p2);
- *   accept iff max(tmin, 0) <= t <= tmax: hits behind the origin are never
- *   reported (the paper's slab test clamps the entry distance with max(0, .)
- *   and its triangle test requires t > 0, App. G); a NaN tmin counts as 0. */
+ *   accept iff max(tmin, 0) <= t <= tmax. The interval is closed at both
+ *   ends, like the ray interval [tmin, tmax] of scion_ray. Its lower end is
+ *   never below 0, so no hit behind the origin is reported, as in App. G,
+ *   whose box test clamps the entry distance with max(0, .). App. G's
+ *   triangle test is strict (t > 0): this reading differs from it only at
+ *   t = 0 exactly, which it accepts when tmin <= 0. A NaN tmin counts as 0. */
 static int tri_test(const float *o, const shear_t *s, float tmin, float tmax,
                     const float *p, float *t_out, float *u_out, float *v_out) {
   if (!tri_finite(p)) return 0;

@@ -75,6 +75,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                  os.path.join(BUILD, "refit.o")])
     jobs.append([NVCC, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, "batched.cu"), "-o",
                  os.path.join(BUILD, "batched.o")])
+    jobs.append([NVCC, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, "membw.cu"), "-o",
+                 os.path.join(BUILD, "membw.o")])
     jobs.append(["g++", *CXX_FLAGS, "-c", os.path.join(CSRC, "builder.cpp"), "-o",
                  os.path.join(BUILD, "builder.o")])
     workers = max(1, min(len(jobs), os.cpu_count() or 1))

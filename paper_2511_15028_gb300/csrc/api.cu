@@ -52,7 +52,8 @@ struct scion_bvh_s {
 
 namespace {
 
-std::string g_last_error;
+// message of the last failing call, per host thread
+thread_local std::string g_last_error;
 constexpr size_t kScratchBytes = 16 + 16 * kStreamSlotCount;
 
 // scion_trace_params.ordered_children -> kernel order mode
@@ -96,32 +97,57 @@ void free_bvh(scion_bvh b) {
   delete b;
 }
 
+int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return dev;
+}
+
+// Device (or managed) memory that a kernel on the current device may use:
+// device memory of another GPU would be a peer access the caller never
+// arranged, so it is refused like host memory.
 bool is_device_ptr(const void *p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == current_device();
 }
 
 // The address a kernel uses for a ray or result buffer: device (or managed)
-// memory as given, page-locked host memory through its device mapping (the
-// kernel then reads and writes host memory directly, e.g. over NVLink-C2C).
-// Pageable host memory is not reachable from a kernel: nullptr.
+// memory of the current device as given, page-locked host memory through its
+// device mapping (the kernel then reads and writes host memory directly, e.g.
+// over NVLink-C2C). Pageable host memory and other GPUs' memory are not
+// reachable from the kernel: nullptr.
 const void *kernel_view(const void *p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeDevice) return at.device == current_device() ? p : nullptr;
   if (at.type == cudaMemoryTypeHost && at.devicePointer) {
     // the mapping of the allocation's start, shifted to p
     const char *base = static_cast<const char *>(at.hostPointer);
     return static_cast<const char *>(at.devicePointer) + (static_cast<const char *>(p) - base);
   }
   return nullptr;
+}
+
+// The BVH's buffers live on the device it was built on; a call made while
+// another device is current would hand them to that device's kernels.
+bool on_bvh_device(const scion_bvh b) {
+  const int dev = current_device();
+  if (dev == b->device) return true;
+  g_last_error = "the BVH was built on device " + std::to_string(b->device) + " but device " +
+                 std::to_string(dev) + " is current";
+  return false;
 }
 
 template <typename T>
@@ -220,33 +246,34 @@ TraceKernel pick_cpq_kernel(const scion_bvh b, int stats) {
   return nullptr;
 }
 
-TraceKernel pick_kernel(const scion_bvh b, int query, int stats) {
+TraceKernel pick_kernel(const scion_bvh b, int query, int stats, uint32_t reg) {
   const scion_layout_desc &d = b->desc;
   const int soa = (int)d.box_layout, cref = (int)d.child_ref;
-  if (query == kQueryPoint) return pick_cpq_kernel(b, stats);
+  if (query == kQueryPoint) return reg == 0 ? pick_cpq_kernel(b, stats) : nullptr;
+  const int rg = (int)reg;
   const int any = query == kQueryAny ? 1 : 0;
   if (b->own_box) {
     switch (d.box_prec) {
-      case PREC_F32: return kernels_own_p0(soa, cref, any, stats);
-      case PREC_Q16: return kernels_own_p3(soa, cref, any, stats);
-      case PREC_EQ10: return kernels_own_p4(soa, cref, any, stats);
-      case PREC_SLAB: return kernels_own_p6(soa, cref, any, stats);
+      case PREC_F32: return kernels_own_p0(soa, cref, any, stats, rg);
+      case PREC_Q16: return kernels_own_p3(soa, cref, any, stats, rg);
+      case PREC_EQ10: return kernels_own_p4(soa, cref, any, stats, rg);
+      case PREC_SLAB: return kernels_own_p6(soa, cref, any, stats, rg);
     }
     return nullptr;
   }
   switch (d.width * 10 + d.box_prec) {
-    case 20: return kernels_w2_p0(soa, cref, any, stats);
-    case 21: return kernels_w2_p1(soa, cref, any, stats);
-    case 22: return kernels_w2_p2(soa, cref, any, stats);
-    case 40: return kernels_w4_p0(soa, cref, any, stats);
-    case 41: return kernels_w4_p1(soa, cref, any, stats);
-    case 42: return kernels_w4_p2(soa, cref, any, stats);
-    case 80: return kernels_w8_p0(soa, cref, any, stats);
-    case 81: return kernels_w8_p1(soa, cref, any, stats);
-    case 82: return kernels_w8_p2(soa, cref, any, stats);
-    case 25: return kernels_w2_p5(soa, cref, any, stats);
-    case 45: return kernels_w4_p5(soa, cref, any, stats);
-    case 85: return kernels_w8_p5(soa, cref, any, stats);
+    case 20: return kernels_w2_p0(soa, cref, any, stats, rg);
+    case 21: return kernels_w2_p1(soa, cref, any, stats, rg);
+    case 22: return kernels_w2_p2(soa, cref, any, stats, rg);
+    case 40: return kernels_w4_p0(soa, cref, any, stats, rg);
+    case 41: return kernels_w4_p1(soa, cref, any, stats, rg);
+    case 42: return kernels_w4_p2(soa, cref, any, stats, rg);
+    case 80: return kernels_w8_p0(soa, cref, any, stats, rg);
+    case 81: return kernels_w8_p1(soa, cref, any, stats, rg);
+    case 82: return kernels_w8_p2(soa, cref, any, stats, rg);
+    case 25: return kernels_w2_p5(soa, cref, any, stats, rg);
+    case 45: return kernels_w4_p5(soa, cref, any, stats, rg);
+    case 85: return kernels_w8_p5(soa, cref, any, stats, rg);
   }
   return nullptr;
 }
@@ -355,18 +382,83 @@ int device_sms(int dev) {
   return g_dev[dev].sms;
 }
 
-scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *out,
-                          const scion_trace_params *params, cudaStream_t stream, int query,
-                          unsigned long long *stats = nullptr) {
-  if (!b || (n > 0 && (!rays || !out))) return SCION_ERR_INVALID_ARG;
-  if (n == 0) return SCION_OK;
+// Resident CTAs per SM of a kernel at a launch shape, per device: the
+// occupancy query (and the large-shared-memory opt-in) runs once per
+// (kernel, threads, shared bytes, device), not on every trace call.
+struct OccKey {
+  const void *k;
+  uint32_t tpb;
+  size_t smem;
+  int dev;
+  int ctas;
+};
+std::mutex g_occ_mu;
+std::vector<OccKey> g_occ;
+
+scion_status ctas_per_sm(const void *k, uint32_t tpb, size_t smem, int dev, uint32_t *out) {
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    for (const OccKey &o : g_occ)
+      if (o.k == k && o.tpb == tpb && o.smem == smem && o.dev == dev) {
+        *out = (uint32_t)o.ctas;
+        return SCION_OK;
+      }
+  }
+  if (smem > kSmemOptIn)
+    SCION_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nb = 0;
+  SCION_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, (int)tpb, smem));
+  nb = std::max(nb, 1);
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ.push_back(OccKey{k, tpb, smem, dev, nb});
+  *out = (uint32_t)nb;
+  return SCION_OK;
+}
+
+// A trace launch ready to go, but for the counters it uses.
+struct TraceLaunch {
+  TraceKernel k = nullptr;
+  TraceArgs a{};
+  uint32_t tpb = 0;
+  size_t smem = 0;
+  uint64_t grid = 0;
+  uint32_t ctas_param = 0;  // scion_trace_params.ctas_per_sm (0: from occupancy)
+  uint32_t reg_stack = 0;   // register entries at the top of the stack
+};
+
+// Checks and set-up shared by every entry point that launches a traversal or
+// closest point kernel (scion_trace_closest/_any/_stats,
+// scion_query_closest_point, scion_trace_closest_noalloc): arguments,
+// alignment, traversal parameters, the device, and the buffers a kernel can
+// reach. On success `L` holds everything but the work counters and the
+// visit counters; on failure nothing has been issued and g_last_error says
+// why. n must be > 0.
+scion_status prepare_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *out,
+                           const scion_trace_params *params, int query, TraceLaunch *L) {
+  if (!b || !rays || !out) {
+    g_last_error = "null BVH, input or result buffer";
+    return SCION_ERR_INVALID_ARG;
+  }
   const bool out16 = query != kQueryAny;  // scion_hit / scion_closest_point records
   if ((reinterpret_cast<uintptr_t>(rays) & 15u) || (out16 && (reinterpret_cast<uintptr_t>(out) & 15u)) ||
-      (!out16 && (reinterpret_cast<uintptr_t>(out) & 3u)))
+      (!out16 && (reinterpret_cast<uintptr_t>(out) & 3u))) {
+    g_last_error = "input records must be 16-byte aligned, results 16-byte (records) or 4-byte (flags) aligned";
     return SCION_ERR_INVALID_ARG;
+  }
   scion_trace_params p{};
   if (params) p = *params;
-  if (p.reg_stack != 0 || p.rays_per_fetch > 32) return SCION_ERR_INVALID_ARG;
+  if (p.reg_stack != 0 && p.reg_stack != 2 && p.reg_stack != kMaxRegStack) {
+    g_last_error = "reg_stack must be 0, 2 or 4";
+    return SCION_ERR_INVALID_ARG;
+  }
+  if (query == kQueryPoint && p.reg_stack != 0) {
+    g_last_error = "closest point queries keep their stack in memory (reg_stack 0)";
+    return SCION_ERR_INVALID_ARG;
+  }
+  if (p.rays_per_fetch > 32) {
+    g_last_error = "rays_per_fetch exceeds 32";
+    return SCION_ERR_INVALID_ARG;
+  }
   if (p.raster_width != 0 && ((p.rays_per_fetch != 0 && p.rays_per_fetch != 32) || query == kQueryPoint)) {
     g_last_error = "raster_width needs warp batches (rays_per_fetch 0 or 32) and rays";
     return SCION_ERR_INVALID_ARG;
@@ -375,55 +467,96 @@ scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *
     g_last_error = "closest point queries take 32-point warp batches only (rays_per_fetch 0 or 32)";
     return SCION_ERR_INVALID_ARG;
   }
-  uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
-  if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
-  uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
-  if (smem_entries > 64) return SCION_ERR_INVALID_ARG;
-  smem_entries = stack_entries(b, smem_entries, query);
-  if (p.ordered_children > 3) return SCION_ERR_INVALID_ARG;
-  const uint32_t ordered = order_mode(p.ordered_children);
-  TraceKernel k = pick_kernel(b, query, stats ? 1 : 0);
-  if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
-  const size_t smem = (size_t)tpb * smem_entries * stack_entry_bytes(b, query);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  uint32_t ctas = p.ctas_per_sm;
-  if (ctas == 0) {
-    int nb = 0;
-    SCION_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k, (int)tpb, smem));
-    ctas = (uint32_t)std::max(nb, 1);
-  }
-  if (smem > kSmemOptIn)
-    SCION_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
-  TraceArgs a;
-  bvh_args(b, a);
-  const void *k_rays = kernel_view(rays), *k_out = kernel_view(out);
-  if (!k_rays || !k_out) {
-    g_last_error = "ray and result buffers must be device memory or page-locked host memory";
+  const uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
+  if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) {
+    g_last_error = "threads_per_block must be a multiple of 32 and at most " + std::to_string(kMaxThreadsPerBlock);
     return SCION_ERR_INVALID_ARG;
   }
+  uint32_t smem_entries = p.smem_stack ? p.smem_stack : 16;
+  if (smem_entries > 64) {
+    g_last_error = "smem_stack exceeds 64 entries";
+    return SCION_ERR_INVALID_ARG;
+  }
+  smem_entries = stack_entries(b, smem_entries, query);
+  if (p.ordered_children > 3) {
+    g_last_error = "ordered_children must be 0..3";
+    return SCION_ERR_INVALID_ARG;
+  }
+  if (!on_bvh_device(b)) return SCION_ERR_INVALID_ARG;
+  TraceKernel k = pick_kernel(b, query, 0, p.reg_stack);
+  if (!k) {
+    g_last_error = "this query is not offered for the BVH's layout";
+    return SCION_ERR_UNSUPPORTED_LAYOUT;
+  }
+  const void *k_rays = kernel_view(rays), *k_out = kernel_view(out);
+  if (!k_rays || !k_out) {
+    g_last_error = "input and result buffers must be device memory of the current device or page-locked host memory";
+    return SCION_ERR_INVALID_ARG;
+  }
+  L->k = k;
+  L->tpb = tpb;
+  L->smem = (size_t)tpb * smem_entries * stack_entry_bytes(b, query);
+  TraceArgs &a = L->a;
+  bvh_args(b, a);
   a.rays = reinterpret_cast<const float4 *>(k_rays);
   a.out = const_cast<void *>(k_out);
   a.n = n;
   a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
-  a.ordered = ordered;
+  a.ordered = order_mode(p.ordered_children);
   a.smem_stack = smem_entries;
   a.refill_min = p.rays_per_fetch < 32 ? p.rays_per_fetch : 0u;
   set_raster(a, p.raster_width);
+  a.status = b->d_scratch + 3;
+  a.stats = nullptr;
+  a.work = nullptr;
+  a.exit_count = nullptr;
+  L->ctas_param = p.ctas_per_sm;
+  L->reg_stack = p.reg_stack;
+  return SCION_OK;
+}
+
+// Grid of a prepared launch (persistent CTAs per SM x SMs, at most one CTA
+// per tpb rays) and the launch itself.
+scion_status issue_trace(TraceLaunch &L, cudaStream_t stream, TraceKernel k) {
+  const int dev = current_device();
+  uint32_t ctas = L.ctas_param;
+  if (ctas == 0) {
+    scion_status st = ctas_per_sm((const void *)k, L.tpb, L.smem, dev, &ctas);
+    if (st != SCION_OK) return st;
+  } else if (L.smem > kSmemOptIn) {
+    uint32_t ignored = 0;
+    scion_status st = ctas_per_sm((const void *)k, L.tpb, L.smem, dev, &ignored);  // the opt-in
+    if (st != SCION_OK) return st;
+  }
+  L.grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (L.a.n + L.tpb - 1) / L.tpb);
+  void *args[] = {&L.a};
+  SCION_CUDA(cudaLaunchKernel((const void *)k, dim3((unsigned)L.grid), dim3(L.tpb), args, L.smem, stream));
+  return SCION_OK;
+}
+
+scion_status launch_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void *out,
+                          const scion_trace_params *params, cudaStream_t stream, int query,
+                          unsigned long long *stats = nullptr) {
+  if (!b) return SCION_ERR_INVALID_ARG;
+  if (n == 0) return SCION_OK;
+  TraceLaunch L;
+  scion_status st = prepare_trace(b, rays, n, out, params, query, &L);
+  if (st != SCION_OK) return st;
+  TraceKernel k = L.k;
+  if (stats) {
+    k = pick_kernel(b, query, 1, 0);
+    if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
+  }
   const int slot = stream_slot(b, stream);
   if (slot < 0) {
     g_last_error = "more than 64 streams have traced this BVH";
     return SCION_ERR_INVALID_ARG;
   }
   uint32_t *sl = b->d_scratch + 4 + 4 * slot;
-  a.work = reinterpret_cast<unsigned long long *>(sl);
-  a.exit_count = sl + 2;
-  a.status = b->d_scratch + 3;
-  a.stats = stats;
-  void *args[] = {&a};
-  SCION_CUDA(cudaLaunchKernel((const void *)k, dim3((unsigned)grid), dim3(tpb), args, smem, stream));
-  return SCION_OK;
+  L.a.work = reinterpret_cast<unsigned long long *>(sl);
+  L.a.exit_count = sl + 2;
+  L.a.stats = stats;
+  return issue_trace(L, stream, k);
 }
 
 
@@ -593,6 +726,7 @@ scion_status scion_refit(scion_bvh bvh, const float *d_verts, uint64_t n_verts, 
     g_last_error = "scion_refit: vertices must be device memory";
     return SCION_ERR_INVALID_ARG;
   }
+  if (!on_bvh_device(bvh)) return SCION_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   scion_bvh b = bvh;
   if (!b->d_refit_parent && b->n_nodes > 0) {
@@ -722,8 +856,11 @@ scion_status scion_trace_backward(scion_bvh b, const scion_ray *d_rays, const sc
   if (n == 0) return SCION_OK;
   if ((reinterpret_cast<uintptr_t>(d_rays) & 15u) || (reinterpret_cast<uintptr_t>(d_hits) & 15u) ||
       (reinterpret_cast<uintptr_t>(d_grad_rays) & 15u) || (reinterpret_cast<uintptr_t>(d_grad_tuv) & 3u) ||
-      (reinterpret_cast<uintptr_t>(d_grad_verts) & 3u))
+      (reinterpret_cast<uintptr_t>(d_grad_verts) & 3u)) {
+    g_last_error = "scion_trace_backward: misaligned buffer";
     return SCION_ERR_INVALID_ARG;
+  }
+  if (!on_bvh_device(b)) return SCION_ERR_INVALID_ARG;
   // the kernel scatters into the gradients with device atomics: device memory only
   if (!is_device_ptr(d_rays) || !is_device_ptr(d_hits) || !is_device_ptr(d_grad_tuv) ||
       !is_device_ptr(d_grad_verts) || (d_grad_rays && !is_device_ptr(d_grad_rays))) {
@@ -789,6 +926,10 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
       return SCION_ERR_INVALID_ARG;
     }
     if (n[i] == 0) continue;
+    if (!on_bvh_device(b)) {
+      delete bt;
+      return SCION_ERR_INVALID_ARG;
+    }
     const void *k_rays = kernel_view(d_rays[i]), *k_hits = kernel_view(d_hits[i]);
     if (!k_rays || !k_hits) {
       g_last_error = "ray and result buffers must be device memory or page-locked host memory";
@@ -1071,63 +1212,24 @@ scion_status static_scratch(void **out) {
 extern "C" scion_status scion_trace_closest_noalloc(scion_bvh b, const scion_ray *rays, uint64_t n,
                                                     scion_hit *hits, const scion_trace_params *params,
                                                     scion_stream stream) {
-  if (!b || (n > 0 && (!rays || !hits))) return SCION_ERR_INVALID_ARG;
+  if (!b) return SCION_ERR_INVALID_ARG;
   if (n >= kStaticMaxRays) {
     g_last_error = "scion_trace_closest_noalloc: n exceeds the static scratch counter range (2^62 rays)";
     return SCION_ERR_INVALID_ARG;
   }
   if (n == 0) return SCION_OK;
-  if ((reinterpret_cast<uintptr_t>(rays) & 15u) || (reinterpret_cast<uintptr_t>(hits) & 15u))
-    return SCION_ERR_INVALID_ARG;
-  scion_trace_params p{};
-  if (params) p = *params;
-  if (p.reg_stack != 0 || p.rays_per_fetch > 32 || p.ordered_children > 3 ||
-      (p.raster_width != 0 && p.rays_per_fetch != 0 && p.rays_per_fetch != 32))
-    return SCION_ERR_INVALID_ARG;
-  const uint32_t tpb = p.threads_per_block ? p.threads_per_block : 256;
-  if (tpb % 32 || tpb > (uint32_t)kMaxThreadsPerBlock) return SCION_ERR_INVALID_ARG;
-  if ((p.smem_stack ? p.smem_stack : 16) > 64) return SCION_ERR_INVALID_ARG;
-  const uint32_t smem_entries = stack_entries(b, p.smem_stack ? p.smem_stack : 16, kQueryClosest);
-  TraceKernel k = pick_kernel(b, kQueryClosest, 0);
-  if (!k) return SCION_ERR_UNSUPPORTED_LAYOUT;
-  const void *k_rays = kernel_view(rays), *k_hits = kernel_view(hits);
-  if (!k_rays || !k_hits) {
-    g_last_error = "ray and result buffers must be device memory or page-locked host memory";
-    return SCION_ERR_INVALID_ARG;
-  }
+  // the same checks and set-up as scion_trace_closest, then the counters of
+  // the static array instead of the BVH's
+  TraceLaunch L;
+  scion_status st = prepare_trace(b, rays, n, hits, params, kQueryClosest, &L);
+  if (st != SCION_OK) return st;
   void *scratch = nullptr;
-  scion_status st = static_scratch(&scratch);
+  st = static_scratch(&scratch);
   if (st != SCION_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // the counters must start at zero; they keep the previous call's values
   SCION_CUDA(cudaMemsetAsync(scratch, 0, kStaticScratchUsed, s));
-  const size_t smem = (size_t)tpb * smem_entries * stack_entry_bytes(b, kQueryClosest);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  uint32_t ctas = p.ctas_per_sm;
-  if (ctas == 0) {
-    int nb = 0;
-    SCION_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k, (int)tpb, smem));
-    ctas = (uint32_t)std::max(nb, 1);
-  }
-  if (smem > kSmemOptIn)
-    SCION_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const uint64_t grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (n + tpb - 1) / tpb);
-  TraceArgs a;
-  bvh_args(b, a);
-  a.rays = reinterpret_cast<const float4 *>(k_rays);
-  a.out = const_cast<void *>(k_hits);
-  a.n = n;
-  a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
-  a.ordered = order_mode(p.ordered_children);
-  a.smem_stack = smem_entries;
-  a.refill_min = p.rays_per_fetch < 32 ? p.rays_per_fetch : 0u;
-  set_raster(a, p.raster_width);
-  a.work = static_cast<unsigned long long *>(scratch);
-  a.exit_count = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(scratch) + 8);
-  a.status = b->d_scratch + 3;  // device errors still go to the BVH's status word
-  a.stats = nullptr;
-  void *args[] = {&a};
-  SCION_CUDA(cudaLaunchKernel((const void *)k, dim3((unsigned)grid), dim3(tpb), args, smem, s));
-  return SCION_OK;
+  L.a.work = static_cast<unsigned long long *>(scratch);
+  L.a.exit_count = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(scratch) + 8);
+  return issue_trace(L, s, L.k);  // device errors still go to the BVH's status word
 }

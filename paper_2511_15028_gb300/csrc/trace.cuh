@@ -244,30 +244,45 @@ __device__ __forceinline__ uint32_t qword(const uint4 (&q)[NQ], int i) {
 // Entries (ref, entry distance); with TF also the exit distance of the
 // entry's interval (the shared-slab traversal carries intervals, not boxes),
 // in a second shared-memory column.
-template <bool TF, bool RING = false>
+//
+// Three tiers, newest entries first: R entries in registers (R = 0, 2 or 4,
+// the traversal parameter reg_stack), then cap_sh entries in this thread's
+// shared-memory column, then a local-memory tail. The register tier is a
+// shift register (rr[0] newest; pushes and pops move every register entry,
+// so each index is a compile-time constant and the entries stay in
+// registers); when it is full, a push moves its oldest entry into shared
+// memory. Pops take the register entries first and only then read memory.
+template <bool TF, bool RING = false, int R = 0>
 struct StackT {
   uint2 *sh;      // this thread's column in shared memory
   float *shf;     // exit distances (TF)
   int stride;     // blockDim.x
   int cap_sh;     // entries in shared memory (RING: a power of two)
-  int sp;         // entries on the stack
+  int sp;         // entries in memory (shared + local)
   int base;       // RING: entries [0, base) are in local memory, [base, sp) in shared memory
+  int rn;         // entries in registers
   float ptf;      // exit distance of the last popped entry (TF)
+  uint32_t rr[R > 0 ? R : 1];
+  float rt[R > 0 ? R : 1];
+  float rf[(R > 0 && TF) ? R : 1];
   uint2 loc[kLocalStack];
   float locf[TF ? kLocalStack : 1];
+  static constexpr int kRegs = R;
 
-  // Without RING the first cap_sh entries live in shared memory and deeper
-  // ones in local memory. With RING the shared part holds the cap_sh most
-  // recent entries: when it is full the oldest one moves to local memory,
-  // which is read again only once the shared part is empty, so pushes and
-  // pops near the top stay in shared memory however deep the stack grows.
+  // Without RING the first cap_sh memory entries live in shared memory and
+  // deeper ones in local memory. With RING the shared part holds the cap_sh
+  // most recent memory entries: when it is full the oldest one moves to
+  // local memory, which is read again only once the shared part is empty, so
+  // pushes and pops near the top stay in shared memory however deep the
+  // stack grows.
   __device__ __forceinline__ int slot(int i) const { return (RING ? (i & (cap_sh - 1)) : i) * stride; }
   __device__ __forceinline__ void reset() {
     sp = 0;
     base = 0;
+    rn = 0;
   }
-  __device__ __forceinline__ bool push(uint32_t ref, float tn, float tf = 0.f) {
-    const uint2 e = make_uint2(ref, __float_as_uint(tn));
+  __device__ __forceinline__ bool empty() const { return sp + rn == 0; }
+  __device__ __forceinline__ bool mem_push(uint2 e, float tf) {
     if constexpr (RING) {
       if (sp - base == cap_sh) {
         if (base == kLocalStack) return false;
@@ -291,7 +306,7 @@ struct StackT {
     ++sp;
     return true;
   }
-  __device__ __forceinline__ uint2 pop() {
+  __device__ __forceinline__ uint2 mem_pop() {
     --sp;
     if constexpr (RING) {
       if (sp >= base) {
@@ -309,6 +324,45 @@ struct StackT {
       if (TF) ptf = locf[sp - cap_sh];
       return loc[sp - cap_sh];
     }
+  }
+  __device__ __forceinline__ bool push(uint32_t ref, float tn, float tf = 0.f) {
+    if constexpr (R > 0) {
+      if (rn == R) {
+        if (!mem_push(make_uint2(rr[R - 1], __float_as_uint(rt[R - 1])), TF ? rf[R - 1] : 0.f)) return false;
+      } else {
+        ++rn;
+      }
+#pragma unroll
+      for (int i = R - 1; i > 0; --i) {
+        rr[i] = rr[i - 1];
+        rt[i] = rt[i - 1];
+        if (TF) rf[i] = rf[i - 1];
+      }
+      rr[0] = ref;
+      rt[0] = tn;
+      if (TF) rf[0] = tf;
+      return true;
+    } else {
+      return mem_push(make_uint2(ref, __float_as_uint(tn)), tf);
+    }
+  }
+  // Only when !empty().
+  __device__ __forceinline__ uint2 pop() {
+    if constexpr (R > 0) {
+      if (rn > 0) {
+        const uint2 e = make_uint2(rr[0], __float_as_uint(rt[0]));
+        if (TF) ptf = rf[0];
+#pragma unroll
+        for (int i = 0; i + 1 < R; ++i) {
+          rr[i] = rr[i + 1];
+          rt[i] = rt[i + 1];
+          if (TF) rf[i] = rf[i + 1];
+        }
+        --rn;
+        return e;
+      }
+    }
+    return mem_pop();
   }
 };
 using Stack = StackT<false>;
@@ -419,7 +473,7 @@ struct Lane {
 // stacked entry (any-hit); kEmptyRef when the stack is exhausted.
 template <bool ANY, class S>
 __device__ __forceinline__ uint32_t pop_next(S &st, float best_t, float &tn) {
-  while (st.sp > 0) {
+  while (!st.empty()) {
     const uint2 e = st.pop();
     tn = __uint_as_float(e.y);
     if (ANY || tn <= best_t) return e.x;
@@ -588,7 +642,7 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Co
     // push every hit child but the first, last one first; go on with the first
     uint32_t next = kEmptyRef;
     float next_tn = 0.f;
-    if (st.sp - st.base + W <= st.cap_sh) {
+    if (S::kRegs == 0 && st.sp - st.base + W <= st.cap_sh) {
       // room in shared memory for any node: predicated stores, one check
       int sp = st.sp;
 #pragma unroll
@@ -718,7 +772,7 @@ __device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, S &st, Cou
       return;
     }
   }
-  L.cur = st.sp > 0 ? st.pop().x : kEmptyRef;
+  L.cur = !st.empty() ? st.pop().x : kEmptyRef;
 }
 
 // Shared-slab binary node (Section 8.3): the node's box is not stored; the
@@ -727,9 +781,9 @@ __device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, S &st, Cou
 // the left child's upper bound on the split axis, shi: the right child's
 // lower bound), widened like every slab distance. Stacked entries keep their
 // interval.
-template <bool ANY>
-__device__ __forceinline__ void slab_pop(Lane &L, StackT<true> &st) {
-  while (st.sp > 0) {
+template <bool ANY, class S>
+__device__ __forceinline__ void slab_pop(Lane &L, S &st) {
+  while (!st.empty()) {
     const uint2 e = st.pop();
     const float tn = __uint_as_float(e.y);
     if (ANY || tn <= L.b.t) {
@@ -742,8 +796,8 @@ __device__ __forceinline__ void slab_pop(Lane &L, StackT<true> &st) {
   L.cur = kEmptyRef;
 }
 
-template <int CREF, bool ANY, bool STATS>
-__device__ __forceinline__ void step_slab(const TraceArgs &a, Lane &L, StackT<true> &st, Counts &cnt) {
+template <int CREF, bool ANY, bool STATS, class S>
+__device__ __forceinline__ void step_slab(const TraceArgs &a, Lane &L, S &st, Counts &cnt) {
   const Ray &r = L.r;
   const uint32_t cur = L.cur;
   if (STATS) cnt.nodes++;
@@ -811,8 +865,8 @@ __device__ __forceinline__ void start_ray(const TraceArgs &a, Lane &L) {
 // The ring pays for its extra register where the kernel has room: the own-box
 // bvh2 kernels (all but the shared slab) and the any-hit kernels of nodes up to
 // 4 wide; in the other 64-register kernels it would spill.
-template <bool OWN, int PREC, int W, bool ANY>
-using StackFor = StackT<OWN && PREC == PREC_SLAB, (OWN && PREC != PREC_SLAB) || (!OWN && ANY && W <= 4)>;
+template <bool OWN, int PREC, int W, bool ANY, int REG>
+using StackFor = StackT<OWN && PREC == PREC_SLAB, (OWN && PREC != PREC_SLAB) || (!OWN && ANY && W <= 4), REG>;
 
 // ------------------------------------------------------------------ kernel body
 // Trace one ray to completion with the layout's step function.
@@ -850,7 +904,7 @@ __device__ __forceinline__ void body_warp_batch(const TraceArgs &a, S &st) {
     unsigned long long rid = base + lane;
     if (a.raster_w) {
       // slot batch t is the 8x4 pixel tile (t mod tiles_x, t / tiles_x)
-      const unsigned long long t = base >> 5, tiles_x = (a.raster_w + 7u) >> 3;
+      const unsigned long long t = base >> 5, tiles_x = (a.raster_w + 7ull) >> 3;  // 64-bit: no wrap near 2^32
       const unsigned long long px = (t % tiles_x) * 8u + (lane & 7u), py = (t / tiles_x) * 4u + (lane >> 3);
       rid = px < a.raster_w ? py * a.raster_w + px : a.n;
     }
@@ -974,10 +1028,11 @@ __device__ __forceinline__ void body_refill(const TraceArgs &a, S &st) {
 }
 
 
-template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS>
+// REG: register entries at the top of the stack (0, 2 or 4).
+template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS, int REG = 0>
 __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
   extern __shared__ uint2 smem_stack[];
-  StackFor<OWN, PREC, W, ANY> st;
+  StackFor<OWN, PREC, W, ANY, REG> st;
   st.sh = smem_stack + threadIdx.x;
   // exit distances (shared-slab layout) follow the entry columns
   st.shf = reinterpret_cast<float *>(smem_stack + blockDim.x * a.smem_stack) + threadIdx.x;

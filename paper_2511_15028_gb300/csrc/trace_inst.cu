@@ -21,22 +21,39 @@ namespace scion {
 #define SCION_CPQ_GETTER SCION_CAT(SCION_CAT(SCION_CAT(cpq_kernels_w, SCION_W), _p), SCION_PREC)
 #endif
 
-template <int SOA, int CREF, bool ANY, bool STATS>
-__global__ void __launch_bounds__(kMaxThreadsPerBlock, kMinBlocksPerSm) trace_kernel(TraceArgs a) {
-  trace_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, ANY, STATS>(a);
+// The register tier of the stack needs registers the 64-register cap of four
+// CTAs per SM does not leave (it would spill): three CTAs per SM for it.
+template <int SOA, int CREF, bool ANY, bool STATS, int REG>
+__global__ void __launch_bounds__(kMaxThreadsPerBlock, REG > 0 && kMinBlocksPerSm > 3 ? 3 : kMinBlocksPerSm)
+    trace_kernel(TraceArgs a) {
+  trace_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, ANY, STATS, REG>(a);
 }
 
-TraceKernel SCION_GETTER(int soa, int cref, int any, int stats) {
-  static const TraceKernel table[2][2][2][2] = {
-      {{{trace_kernel<0, 0, false, false>, trace_kernel<0, 0, false, true>},
-        {trace_kernel<0, 0, true, false>, trace_kernel<0, 0, true, true>}},
-       {{trace_kernel<0, 1, false, false>, trace_kernel<0, 1, false, true>},
-        {trace_kernel<0, 1, true, false>, trace_kernel<0, 1, true, true>}}},
-      {{{trace_kernel<1, 0, false, false>, trace_kernel<1, 0, false, true>},
-        {trace_kernel<1, 0, true, false>, trace_kernel<1, 0, true, true>}},
-       {{trace_kernel<1, 1, false, false>, trace_kernel<1, 1, false, true>},
-        {trace_kernel<1, 1, true, false>, trace_kernel<1, 1, true, true>}}}};
-  return table[soa & 1][cref & 1][any & 1][stats & 1];
+// reg: register entries at the top of the stack, 0, 2 or 4 (the counting
+// variants visit the same nodes whatever the stack: they exist for reg 0)
+TraceKernel SCION_GETTER(int soa, int cref, int any, int stats, int reg) {
+  static const TraceKernel counting[2][2][2] = {
+      {{trace_kernel<0, 0, false, true, 0>, trace_kernel<0, 0, true, true, 0>},
+       {trace_kernel<0, 1, false, true, 0>, trace_kernel<0, 1, true, true, 0>}},
+      {{trace_kernel<1, 0, false, true, 0>, trace_kernel<1, 0, true, true, 0>},
+       {trace_kernel<1, 1, false, true, 0>, trace_kernel<1, 1, true, true, 0>}}};
+  static const TraceKernel plain[3][2][2][2] = {
+      {{{trace_kernel<0, 0, false, false, 0>, trace_kernel<0, 0, true, false, 0>},
+        {trace_kernel<0, 1, false, false, 0>, trace_kernel<0, 1, true, false, 0>}},
+       {{trace_kernel<1, 0, false, false, 0>, trace_kernel<1, 0, true, false, 0>},
+        {trace_kernel<1, 1, false, false, 0>, trace_kernel<1, 1, true, false, 0>}}},
+      {{{trace_kernel<0, 0, false, false, 2>, trace_kernel<0, 0, true, false, 2>},
+        {trace_kernel<0, 1, false, false, 2>, trace_kernel<0, 1, true, false, 2>}},
+       {{trace_kernel<1, 0, false, false, 2>, trace_kernel<1, 0, true, false, 2>},
+        {trace_kernel<1, 1, false, false, 2>, trace_kernel<1, 1, true, false, 2>}}},
+      {{{trace_kernel<0, 0, false, false, 4>, trace_kernel<0, 0, true, false, 4>},
+        {trace_kernel<0, 1, false, false, 4>, trace_kernel<0, 1, true, false, 4>}},
+       {{trace_kernel<1, 0, false, false, 4>, trace_kernel<1, 0, true, false, 4>},
+        {trace_kernel<1, 1, false, false, 4>, trace_kernel<1, 1, true, false, 4>}}}};
+  if (stats) return counting[soa & 1][cref & 1][any & 1];
+  const int ri = reg == 4 ? 2 : (reg == 2 ? 1 : 0);
+  if (reg != 0 && reg != 2 && reg != 4) return nullptr;
+  return plain[ri][soa & 1][cref & 1][any & 1];
 }
 
 

@@ -163,6 +163,8 @@ def lib():
         L.scion_debug_f16_round.restype = U32
         L.scion_debug_raster_slots.argtypes = [U64, U32]
         L.scion_debug_raster_slots.restype = U64
+        L.scion_debug_read_bandwidth.argtypes = [P, U64, U32, P, P]
+        L.scion_debug_read_bandwidth.restype = I
         L.scion_debug_f16_decode.argtypes = [U32]
         L.scion_debug_f16_decode.restype = ctypes.c_float
         for name in ("scion_build", "scion_build_gpu", "scion_bvh_build_times", "scion_refit",
@@ -728,6 +730,20 @@ def scion_debug_build_host(verts, desc: LayoutDesc, indices=None) -> HostDecode:
     return HostDecode(info, kind.reshape(nn, 8), a.reshape(nn, 8), c.reshape(nn, 8),
                       boxes.reshape(nn, 8, 6), own.reshape(nn, 6), ids[:inf.n_leaf_entries],
                       raw1[:n1], raw2[:inf.node2_bytes], frame)
+
+
+def scion_debug_read_bandwidth(buf, reps: int, sink, stream=None) -> None:
+    """Launch the L2 read probe over the device tensor `buf` (its whole
+    storage, a multiple of 16 bytes) `reps` times; `sink` is a device int32
+    tensor the kernel may write. The caller times the launch."""
+    import torch
+    if not buf.is_cuda or not buf.is_contiguous() or not sink.is_cuda:
+        raise TypeError("scion_debug_read_bandwidth takes contiguous device tensors")
+    nbytes = buf.numel() * buf.element_size()
+    _check(lib().scion_debug_read_bandwidth(ctypes.c_void_p(buf.data_ptr()), nbytes, int(reps),
+                                            ctypes.c_void_p(sink.data_ptr()), _stream_ptr(stream)),
+           "scion_debug_read_bandwidth")
+    del torch
 
 
 def scion_debug_f16_round(x: float, direction: int) -> int:

@@ -111,3 +111,8 @@ def test_camera_ray_tiles_cover_every_ray_once(libscion):
             rid = py * w + px
             hit = rid[(px < w) & (rid < n)]
             assert np.array_equal(np.sort(hit), np.arange(n)), (n, w)
+    # widths next to 2^32, where a 32-bit tile count would wrap to zero: every
+    # ray lies in the first tile row
+    for w in (2**31 + 1, 2**32 - 8, 2**32 - 7, 2**32 - 1):
+        for n in (1, 8, 9, 100):
+            assert libscion.scion_debug_raster_slots(n, w) == 32 * ((n - 1) // 8 + 1), (n, w)

@@ -116,3 +116,48 @@ def test_batched_rejects_camera_ray_tiles(mods):
     with pytest.raises(scion.ScionError) as e:
         scion.Batch(bvhs, rays, params=[dict(raster_width=64), {}])
     assert e.value.status == 1
+
+
+def test_config4_full_size(mods, oracle_mod):
+    """The full batching workload: 64 scenes of 1K-2M triangles with 1K-1M
+    rays each, layouts and parameters picked by the autotuner as the
+    benchmark does, in one launch captured in a CUDA graph. Every hit equals
+    the per-scene plain launch's, and 4,096 sampled rays per scene (all rays
+    of smaller batches) equal the oracle's (brute force where cheap, else its
+    BVH2)."""
+    scion, autotune = mods
+    wl = scenes.config4_workload(seed=1004)
+    assert len(wl) == 64
+    tuner = autotune.Autotuner()
+    chosen, rays = [], []
+    for i, (sc, r) in enumerate(wl):
+        d = torch.from_numpy(r).cuda()
+        chosen.append(tuner.tune(i, sc.verts, sc.indices, d))
+        rays.append(d)
+    bvhs = [c.bvh for c in chosen]
+    params = [c.params for c in chosen]
+    batch = scion.Batch(bvhs, rays, params=params)
+    assert batch.info()["plain_scenes"] == 0
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        batch.launch(stream=s)
+    for h in batch.hits:
+        h.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1404)
+    for i, (sc, r) in enumerate(wl):
+        plain = scion.scion_trace_closest(bvhs[i], rays[i], params=params[i])
+        torch.cuda.synchronize()
+        assert torch.equal(batch.hits[i], plain), f"scene {i}: batched != plain"
+        pick = np.arange(r.shape[0]) if r.shape[0] <= 4096 else np.sort(rng.choice(r.shape[0], 4096, replace=False))
+        tris = sc.triangles()
+        if sc.n_tris * pick.size <= 4e8:
+            exp = oracle_mod.closest_brute(tris, r[pick])
+        else:
+            exp = oracle_mod.BVH2(tris).closest(r[pick])
+        got = scion.split_hits(batch.hits[i])[pick]
+        assert got.tobytes() == exp.tobytes(), f"scene {i} ({sc.name}, {chosen[i].name}) vs oracle"
+        assert scion.scion_get_status(bvhs[i]) == 0

@@ -4,7 +4,9 @@ trace parameters): the coherent+incoherent workload (1,373,138 triangles,
 the incoherent 2^23-triangle soup with 2^23 random rays (closest hit and
 any hit with tmax 0.05). Config-2 outputs are all compared with the CPU
 oracle's BVH2 (bounce and shadow rays come from its own primary hits);
-config-3 outputs on a sample, against brute force."""
+config-3 outputs too (all 2^23 rays of both queries), the oracle's BVH2
+itself being checked against brute force over all 2^23 triangles on 512
+sampled rays of each query."""
 import numpy as np
 import pytest
 
@@ -53,52 +55,61 @@ def test_config2_full_size_all_layouts(sc_mod, oracle_mod):
         assert scion.scion_get_status(bvh) == 0
 
 
-def test_config3_full_size(sc_mod, oracle_mod):
-    """All 2^23 rays are traced on the GPU; 256 sampled rays are checked
-    against brute force over all 2^23 triangles (the definition itself)."""
-    scion = sc_mod
+@pytest.fixture(scope="module")
+def config3(oracle_mod):
+    """The 2^23-triangle soup and rays with the oracle's answers for every
+    ray: its BVH2 traversal over all rays, checked on 512 sampled rays of
+    each query against brute force over every triangle (the definition)."""
     sc = scenes.config3_scene()
     assert sc.n_tris == 1 << 23
     rays = scenes.config3_rays()
     short = rays.copy()
     short[:, 7] = 0.05
-    pick = np.sort(np.random.default_rng(5).choice(rays.shape[0], 256, replace=False))
     tris = sc.verts.reshape(-1, 9)
-    exp = oracle_mod.closest_brute(tris, rays[pick])
-    eocc = oracle_mod.any_brute(tris, short[pick])
+    ob = oracle_mod.BVH2(tris)
+    exp = ob.closest(rays)
+    eocc = ob.any(short)
+    del ob
+    pick = np.sort(np.random.default_rng(5).choice(rays.shape[0], 512, replace=False))
+    brute = oracle_mod.closest_brute(tris, rays[pick])
+    assert brute.tobytes() == exp[pick].tobytes(), "oracle BVH2 vs brute force (closest)"
+    assert np.array_equal(oracle_mod.any_brute(tris, short[pick]), eocc[pick]), "oracle BVH2 vs brute force (any)"
     assert 0.3 < (exp["prim"] != 0xFFFFFFFF).mean() and 0.02 < eocc.mean() < 0.98
+    return sc, rays, short, exp, eocc
+
+
+def test_config3_full_size(sc_mod, config3):
+    """Every swept layout (also in breadth-first order) traces all 2^23 rays
+    (closest hit, and any hit with tmax 0.05); every result equals the
+    oracle's."""
+    scion = sc_mod
+    sc, rays, short, exp, eocc = config3
     d, ds = torch.from_numpy(rays).cuda(), torch.from_numpy(short).cuda()
     for name, desc in scion.sweep_layouts(extended=True, orders=True).items():
         bvh = scion.scion_build(sc.verts, desc)
-        got = scion.scion_trace_closest(bvh, d)[torch.from_numpy(pick).cuda()]
-        _cmp(scion, got, exp, name + " closest")
-        occ = scion.scion_trace_any(bvh, ds).cpu().numpy().astype(np.uint32)[pick]
-        assert np.array_equal(occ, eocc), name + " any"
+        _cmp(scion, scion.scion_trace_closest(bvh, d), exp, name + " closest")
+        occ = scion.scion_trace_any(bvh, ds).cpu().numpy().astype(np.uint32)
+        bad = np.flatnonzero(occ != eocc)
+        assert bad.size == 0, f"{name} any: {bad.size} differ, e.g. {bad[:5]}"
         assert scion.scion_get_status(bvh) == 0
         del bvh
 
 
-def test_config3_full_size_gpu_built(sc_mod, oracle_mod):
+def test_config3_full_size_gpu_built(sc_mod, config3):
     """The 2^23-triangle soup with its logical BVH2 built on the GPU (linear
-    BVH), packed as BVH8 u8 and BVH4: 256 sampled rays against brute force."""
+    BVH), packed as BVH8 u8 and BVH4: all rays against the oracle, also with
+    the newest stack entries in registers."""
     scion = sc_mod
-    sc = scenes.config3_scene()
-    rays = scenes.config3_rays()
-    short = rays.copy()
-    short[:, 7] = 0.05
-    pick = np.sort(np.random.default_rng(6).choice(rays.shape[0], 256, replace=False))
-    tris = sc.verts.reshape(-1, 9)
-    exp = oracle_mod.closest_brute(tris, rays[pick])
-    eocc = oracle_mod.any_brute(tris, short[pick])
+    sc, rays, short, exp, eocc = config3
     d, ds = torch.from_numpy(rays).cuda(), torch.from_numpy(short).cuda()
     dv = torch.from_numpy(sc.verts).cuda()
     for desc in (scion.layout(width=8, box_prec="u8", prim_ref="direct"),
-                 scion.layout(width=4, box_layout="soa", prim_ref="direct")):
+                 scion.layout(width=4, box_layout="soa", prim_ref="direct", order="bfs")):
         bvh = scion.scion_build_gpu(dv, desc)
-        got = scion.scion_trace_closest(bvh, d)[torch.from_numpy(pick).cuda()]
-        _cmp(scion, got, exp, "gpu-built closest")
-        occ = scion.scion_trace_any(bvh, ds).cpu().numpy().astype(np.uint32)[pick]
-        assert np.array_equal(occ, eocc)
+        for p in (None, dict(reg_stack=4, rays_per_fetch=4)):
+            _cmp(scion, scion.scion_trace_closest(bvh, d, params=p), exp, f"gpu-built closest {p}")
+            occ = scion.scion_trace_any(bvh, ds, params=p).cpu().numpy().astype(np.uint32)
+            assert np.array_equal(occ, eocc), f"gpu-built any {p}"
         assert scion.scion_get_status(bvh) == 0
         del bvh
 

@@ -81,6 +81,13 @@ def test_config1_every_layout_bit_exact(sc_mod, config1, kw):
         assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(raster_width=w)), occ)
     assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(rays_per_fetch=1)), occ)
     assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=dict(rays_per_fetch=31)), occ)
+    # the newest stack entries in registers (2 or 4), spilling to a shared
+    # part that is itself tiny (1 entry) or the default, with every fetch mode
+    for p in (dict(reg_stack=2), dict(reg_stack=4, rays_per_fetch=1), dict(reg_stack=4, smem_stack=1),
+              dict(reg_stack=2, smem_stack=1, rays_per_fetch=8, ordered_children=3),
+              dict(reg_stack=4, raster_width=128, ordered_children=2)):
+        assert_same_hits(gpu_closest(sc_mod, bvh, rays, params=p), exp, f"{kw} {p}")
+        assert np.array_equal(gpu_any(sc_mod, bvh, rays, params=p), occ), f"{kw} {p}"
     assert sc_mod.scion_get_status(bvh) == 0
 
 
@@ -198,6 +205,15 @@ def test_device_errors_are_reported_not_faulted(sc_mod):
     assert sc_mod.scion_get_status(b) == 5
     got = gpu_closest(sc_mod, b, ray, params=dict(rays_per_fetch=1))
     assert got["prim"][0] == 0xFFFFFFFE and sc_mod.scion_get_status(b) == 5
+    # four more entries in registers still hold fewer than 100
+    got = gpu_closest(sc_mod, b, ray, params=dict(reg_stack=4))
+    assert got["prim"][0] == 0xFFFFFFFE and sc_mod.scion_get_status(b) == 5
+    for rs in (1, 3, 5, 8):
+        with pytest.raises(sc_mod.ScionError):
+            gpu_closest(sc_mod, bvh, rays, params=dict(reg_stack=rs))
+    with pytest.raises(sc_mod.ScionError):  # closest point queries keep their stack in memory
+        sc_mod.scion_query_closest_point(bvh, torch.zeros((32, 4), dtype=torch.float32, device="cuda"),
+                                         params=dict(reg_stack=2))
     # a short ray that ends before the deep part is unaffected
     ok = gpu_any(sc_mod, b, np.array([[-1.0, 0.0, 0.0, 0.0, -1, 0, 0, np.inf]], np.float32))
     assert ok[0] == 0 and sc_mod.scion_get_status(b) == 0
@@ -241,7 +257,10 @@ def test_random_soup_incoherent(sc_mod, oracle_mod):
                   dict(rays_per_fetch=16, threads_per_block=64), dict(rays_per_fetch=32),
                   # shallow shared stacks: the own-box kernels' ring spills and refills
                   # constantly; 5 and 12 round down to 4 and 8 there
-                  dict(smem_stack=1), dict(smem_stack=5, rays_per_fetch=1), dict(smem_stack=12, ordered_children=3)):
+                  dict(smem_stack=1), dict(smem_stack=5, rays_per_fetch=1), dict(smem_stack=12, ordered_children=3),
+                  # stack entries in registers, spilling into shallow or default shared parts
+                  dict(reg_stack=2), dict(reg_stack=4, rays_per_fetch=4), dict(reg_stack=4, smem_stack=1),
+                  dict(reg_stack=2, smem_stack=5, rays_per_fetch=1, ordered_children=3)):
             assert_same_hits(gpu_closest(sc_mod, bvh, rays, params=p), exp, name + " " + str(p))
             assert np.array_equal(gpu_any(sc_mod, bvh, short, params=p), eocc), name + " " + str(p)
 
