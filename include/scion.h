@@ -368,11 +368,16 @@ scion_status scion_trace_closest_noalloc(scion_bvh bvh, const scion_ray *d_rays,
  * d_hits[i] (scion_hit[n[i]]), both device or page-locked host memory as for
  * scion_trace_closest, per_scene[i] or
  * defaults) into a device table (it allocates and uploads; synchronous on
- * `stream`). threads_per_block and smem_stack are taken from per_scene[0].
+ * `stream`). threads_per_block and smem_stack are taken from per_scene[0];
+ * each scene's ordered_children, rays_per_fetch (warp batches or warp
+ * refill, applied within the 256-ray chunks a warp takes) and max_steps are
+ * its own. raster_width and reg_stack are plain-launch parameters: non-zero
+ * values give SCION_ERR_INVALID_ARG.
  * Scenes whose layout is one of the batched node families (width-2 own-box
- * AoS f32, width-4 SoA f32, width-8 SoA f16, width-8 AoS u8, each with direct
- * child references; triangles direct or indirect) run in one persistent
- * kernel; any other scene gets its own plain launch from scion_batch_launch.
+ * AoS with f32 or q16 boxes, width-4 SoA with f32, f16 or u8 boxes, width-8
+ * SoA f16, width-8 u8 AoS or SoA, each with direct child references;
+ * triangles direct or indirect) run in one persistent kernel; any other scene
+ * gets its own plain launch from scion_batch_launch.
  * The pointers are captured: the buffers must stay valid until the batch is
  * destroyed.
  *

@@ -10,7 +10,8 @@
  *
  * All pointers here are host memory owned by the caller, and none of these
  * calls touches a GPU, except scion_debug_read_bandwidth (a measurement
- * probe, device memory).
+ * probe, device memory), scion_debug_build_gpu_host_pack and
+ * scion_debug_bvh_bytes (the GPU packer's reference and its check).
  */
 #ifndef SCION_DEBUG_H
 #define SCION_DEBUG_H
@@ -93,6 +94,23 @@ uint64_t scion_debug_raster_slots(uint64_t n, uint32_t raster_width);
  * must be device memory of the current device, else SCION_ERR_INVALID_ARG. */
 scion_status scion_debug_read_bandwidth(const void *d_buf, uint64_t bytes, uint32_t reps, uint32_t *d_sink,
                                         scion_stream stream);
+
+/* The GPU construction of scion_build_gpu with the packing done by the host
+ * packers instead of the GPU packer (arguments, errors and result as
+ * scion_build_gpu): the reference against which the GPU packer's bytes are
+ * compared. */
+scion_status scion_debug_build_gpu_host_pack(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices,
+                                             uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
+                                             scion_bvh *out);
+
+/* Host copies of a BVH's packed device buffers: the node array, the second
+ * node array (own-box SoA) and the leaf primitive buffer (48-byte direct
+ * triangles or 4-byte ids). Any destination may be NULL (then only its size
+ * is reported); sizes[0..2] receive the three byte counts. INVALID_ARG if a
+ * given destination is smaller than its buffer. Synchronous (device to
+ * host copies on the legacy default stream). */
+scion_status scion_debug_bvh_bytes(scion_bvh bvh, void *nodes, uint64_t nodes_cap, void *nodes2, uint64_t nodes2_cap,
+                                   void *prims, uint64_t prims_cap, uint64_t *sizes);
 
 /* Message of the last failing call on the calling host thread (kept per
  * thread; valid until that thread's next failing call). */

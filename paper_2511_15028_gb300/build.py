@@ -71,6 +71,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                  os.path.join(BUILD, "backward.o")])
     jobs.append([NVCC, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, "lbvh.cu"), "-o",
                  os.path.join(BUILD, "lbvh.o")])
+    jobs.append([NVCC, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, "gpack.cu"), "-o",
+                 os.path.join(BUILD, "gpack.o")])
     jobs.append([NVCC, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, "refit.cu"), "-o",
                  os.path.join(BUILD, "refit.o")])
     jobs.append([NVCC, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, "batched.cu"), "-o",

@@ -14,6 +14,7 @@
 #include "backward.h"
 #include "batched.h"
 #include "builder.h"
+#include "gpack.h"
 #include "kernels.h"
 #include "lbvh.h"
 #include "refit.h"
@@ -382,9 +383,36 @@ int device_sms(int dev) {
   return g_dev[dev].sms;
 }
 
+// Dynamic shared memory above kSmemOptIn needs the kernel's opt-in
+// attribute. The attribute belongs to the kernel (per device) and only ever
+// grows here: a launch with less shared memory never lowers it below what an
+// earlier launch of the same kernel needed.
+struct SmemKey {
+  const void *k;
+  int dev;
+  size_t bytes;
+};
+std::mutex g_smem_mu;
+std::vector<SmemKey> g_smem;
+
+scion_status ensure_smem_optin(const void *k, size_t smem, int dev) {
+  if (smem <= kSmemOptIn) return SCION_OK;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  for (SmemKey &e : g_smem)
+    if (e.k == k && e.dev == dev) {
+      if (e.bytes >= smem) return SCION_OK;
+      SCION_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      e.bytes = smem;
+      return SCION_OK;
+    }
+  SCION_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  g_smem.push_back(SmemKey{k, dev, smem});
+  return SCION_OK;
+}
+
 // Resident CTAs per SM of a kernel at a launch shape, per device: the
-// occupancy query (and the large-shared-memory opt-in) runs once per
-// (kernel, threads, shared bytes, device), not on every trace call.
+// occupancy query runs once per (kernel, threads, shared bytes, device), not
+// on every trace call.
 struct OccKey {
   const void *k;
   uint32_t tpb;
@@ -404,8 +432,6 @@ scion_status ctas_per_sm(const void *k, uint32_t tpb, size_t smem, int dev, uint
         return SCION_OK;
       }
   }
-  if (smem > kSmemOptIn)
-    SCION_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int nb = 0;
   SCION_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, (int)tpb, smem));
   nb = std::max(nb, 1);
@@ -519,13 +545,11 @@ scion_status prepare_trace(scion_bvh b, const scion_ray *rays, uint64_t n, void 
 // per tpb rays) and the launch itself.
 scion_status issue_trace(TraceLaunch &L, cudaStream_t stream, TraceKernel k) {
   const int dev = current_device();
+  scion_status st = ensure_smem_optin((const void *)k, L.smem, dev);
+  if (st != SCION_OK) return st;
   uint32_t ctas = L.ctas_param;
   if (ctas == 0) {
-    scion_status st = ctas_per_sm((const void *)k, L.tpb, L.smem, dev, &ctas);
-    if (st != SCION_OK) return st;
-  } else if (L.smem > kSmemOptIn) {
-    uint32_t ignored = 0;
-    scion_status st = ctas_per_sm((const void *)k, L.tpb, L.smem, dev, &ignored);  // the opt-in
+    st = ctas_per_sm((const void *)k, L.tpb, L.smem, dev, &ctas);
     if (st != SCION_OK) return st;
   }
   L.grid = std::min<uint64_t>((uint64_t)ctas * device_sms(dev), (L.a.n + L.tpb - 1) / L.tpb);
@@ -605,6 +629,56 @@ scion_status upload_bvh(HostBVH &hb, uint64_t n_tris, uint64_t n_verts, bool ind
   return SCION_OK;
 }
 
+// A BVH around buffers packed on the device (gpu_pack); takes them over.
+scion_status adopt_bvh(DevicePacked &dp, const scion_layout_desc &desc, bool own_box, uint64_t n_tris,
+                       uint64_t n_verts, bool indexed, cudaStream_t s, scion_bvh *out) {
+  auto release = [&]() {
+    void *bufs[] = {dp.nodes, dp.nodes2, dp.prims, dp.prim_ids, dp.verts4, dp.idx};
+    for (void *p : bufs)
+      if (p) cudaFree(p);
+    dp = DevicePacked{};
+  };
+  scion_bvh b = new (std::nothrow) scion_bvh_s();
+  if (!b) {
+    release();
+    return SCION_ERR_OOM;
+  }
+  b->desc = desc;
+  b->own_box = own_box;
+  b->n_tris = (uint32_t)n_tris;
+  b->n_verts = (uint32_t)n_verts;
+  b->indexed = indexed;
+  b->n_nodes = dp.n_nodes;
+  b->node_stride = dp.node_stride;
+  b->n_leaf_entries = dp.n_leaf_entries;
+  b->root_ref = dp.root_ref;
+  b->depth = dp.depth;
+  b->stack_need = dp.stack_need;
+  for (int k = 0; k < 9; ++k) b->frame[k] = dp.frame[k];
+  b->device = current_device();
+  b->d_nodes = dp.nodes;
+  b->d_nodes2 = dp.nodes2;
+  b->d_prims = dp.prims;
+  b->d_prim_ids = dp.prim_ids;
+  b->d_verts = dp.verts4;
+  b->d_idx = dp.idx;
+  b->node_bytes = dp.node_bytes;
+  b->node2_bytes = dp.node2_bytes;
+  b->vert_bytes = dp.vert_bytes;
+  b->idx_bytes = dp.idx_bytes;
+  b->prim_bytes = dp.prim_direct_bytes + dp.prim_id_bytes + (desc.prim_ref == REF_INDIRECT ? dp.idx_bytes : 0);
+  dp = DevicePacked{};  // the BVH owns the buffers now
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_scratch), kScratchBytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scratch, 0, kScratchBytes, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_bvh(b);
+    return e == cudaErrorMemoryAllocation ? SCION_ERR_OOM : cuda_fail(e);
+  }
+  *out = b;
+  return SCION_OK;
+}
+
 // Host copies of device-resident inputs (a device-to-host boundary).
 scion_status host_inputs(const float *verts, uint64_t n_verts, const uint32_t *indices, uint64_t n_tris,
                          cudaStream_t s, std::vector<float> *hv, std::vector<uint32_t> *hi,
@@ -665,23 +739,14 @@ scion_status scion_build(const float *verts, uint64_t n_verts, const uint32_t *i
   return upload_bvh(hb, n_tris, n_verts, ix != nullptr, s, out);
 }
 
-scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices,
-                             uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
-                             scion_bvh *out) {
-  if (!out) return SCION_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (!desc || (n_tris > 0 && !d_verts)) return SCION_ERR_INVALID_ARG;
-  if (n_tris >= kMaxPrims || n_verts >= (1ull << 32)) return SCION_ERR_INVALID_ARG;
-  if (!d_indices && n_verts != 3 * n_tris) return SCION_ERR_INVALID_ARG;
-  if (n_tris > 0 && (!is_device_ptr(d_verts) || (d_indices && !is_device_ptr(d_indices)))) {
-    g_last_error = "scion_build_gpu: vertices and indices must be device memory";
-    return SCION_ERR_INVALID_ARG;
-  }
-  scion_layout_desc d;
-  bool own_box = false;
-  scion_status st = normalize_desc(*desc, &d, &own_box);
-  if (st != SCION_OK) return st;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// GPU construction with packing on the host (the path for the layouts the
+// GPU packer does not build, and a debug entry point that compares the two).
+scion_status build_gpu_host_pack(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices, uint64_t n_tris,
+                                 const scion_layout_desc &d, bool own_box, cudaStream_t s, scion_bvh *out) {
   const auto t0 = std::chrono::steady_clock::now();
   HostBVH hb;
   try {
@@ -691,7 +756,7 @@ scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint3
     std::vector<uint32_t> hi;
     const float *v;
     const uint32_t *ix;
-    st = host_inputs(d_verts, n_verts, d_indices, n_tris, s, &hv, &hi, &v, &ix);
+    scion_status st = host_inputs(d_verts, n_verts, d_indices, n_tris, s, &hv, &hi, &v, &ix);
     if (st != SCION_OK) return st;
     if (ix)
       for (uint64_t i = 0; i < 3 * n_tris; ++i)
@@ -718,6 +783,98 @@ scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint3
   }
   hb.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return upload_bvh(hb, n_tris, n_verts, d_indices != nullptr, s, out);
+}
+
+// Arguments of scion_build_gpu and its debug twin; fills the normalized
+// descriptor.
+scion_status check_build_gpu(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices, uint64_t n_tris,
+                             const scion_layout_desc *desc, scion_bvh *out, scion_layout_desc *d, bool *own_box) {
+  if (!out) return SCION_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc || (n_tris > 0 && !d_verts)) return SCION_ERR_INVALID_ARG;
+  if (n_tris >= kMaxPrims || n_verts >= (1ull << 32)) return SCION_ERR_INVALID_ARG;
+  if (!d_indices && n_verts != 3 * n_tris) return SCION_ERR_INVALID_ARG;
+  if (n_tris > 0 && (!is_device_ptr(d_verts) || (d_indices && !is_device_ptr(d_indices)))) {
+    g_last_error = "scion_build_gpu: vertices and indices must be device memory of the current device";
+    return SCION_ERR_INVALID_ARG;
+  }
+  return normalize_desc(*desc, d, own_box);
+}
+
+}  // namespace
+
+extern "C" {
+
+scion_status scion_build_gpu(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices,
+                             uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
+                             scion_bvh *out) {
+  scion_layout_desc d;
+  bool own_box = false;
+  scion_status st = check_build_gpu(d_verts, n_verts, d_indices, n_tris, desc, out, &d, &own_box);
+  if (st != SCION_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!gpu_pack_supported(d, own_box)) return build_gpu_host_pack(d_verts, n_verts, d_indices, n_tris, d, own_box, s, out);
+  std::string err;
+  bool in_range = true;
+  st = gpu_indices_in_range(d_indices, n_tris, n_verts, s, &in_range, &err);
+  if (st != SCION_OK) {
+    g_last_error = err;
+    return st;
+  }
+  if (!in_range) {
+    g_last_error = "scion_build_gpu: a vertex index is out of range";
+    return SCION_ERR_INVALID_ARG;
+  }
+  LbvhTree t;
+  st = lbvh_build_tree(d_verts, n_verts, d_indices, n_tris, d.leaf_max, s, &t, &err);
+  if (st != SCION_OK) {
+    g_last_error = err;
+    return st;
+  }
+  const auto t1 = std::chrono::steady_clock::now();
+  DevicePacked dp;
+  st = gpu_pack(t, d_verts, n_verts, d_indices, n_tris, d, own_box, s, &dp, &err);
+  if (st != SCION_OK) {
+    g_last_error = err;
+    return st;
+  }
+  const double pack_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+  st = adopt_bvh(dp, d, own_box, n_tris, n_verts, d_indices != nullptr, s, out);
+  if (st != SCION_OK) return st;
+  (*out)->logical_ms = t.gpu_ms;
+  (*out)->pack_ms = pack_ms;
+  (*out)->build_ms = t.gpu_ms + pack_ms;
+  return SCION_OK;
+}
+
+scion_status scion_debug_build_gpu_host_pack(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices,
+                                             uint64_t n_tris, const scion_layout_desc *desc, scion_stream stream,
+                                             scion_bvh *out) {
+  scion_layout_desc d;
+  bool own_box = false;
+  scion_status st = check_build_gpu(d_verts, n_verts, d_indices, n_tris, desc, out, &d, &own_box);
+  if (st != SCION_OK) return st;
+  return build_gpu_host_pack(d_verts, n_verts, d_indices, n_tris, d, own_box, reinterpret_cast<cudaStream_t>(stream),
+                             out);
+}
+
+scion_status scion_debug_bvh_bytes(scion_bvh b, void *nodes, uint64_t nodes_cap, void *nodes2, uint64_t nodes2_cap,
+                                   void *prims, uint64_t prims_cap, uint64_t *sizes) {
+  if (!b || !sizes) return SCION_ERR_INVALID_ARG;
+  const uint64_t pb = b->desc.prim_ref == REF_DIRECT ? 48ull * b->n_leaf_entries : 4ull * b->n_leaf_entries;
+  sizes[0] = b->node_bytes;
+  sizes[1] = b->node2_bytes;
+  sizes[2] = pb;
+  if ((nodes && nodes_cap < b->node_bytes) || (nodes2 && nodes2_cap < b->node2_bytes) || (prims && prims_cap < pb))
+    return SCION_ERR_INVALID_ARG;
+  if (!on_bvh_device(b)) return SCION_ERR_INVALID_ARG;
+  const void *src = b->desc.prim_ref == REF_DIRECT ? b->d_prims : b->d_prim_ids;
+  cudaError_t e = cudaSuccess;
+  if (nodes && b->node_bytes) e = cudaMemcpy(nodes, b->d_nodes, b->node_bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && nodes2 && b->node2_bytes) e = cudaMemcpy(nodes2, b->d_nodes2, b->node2_bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && prims && pb) e = cudaMemcpy(prims, src, pb, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return SCION_OK;
 }
 
 scion_status scion_refit(scion_bvh bvh, const float *d_verts, uint64_t n_verts, scion_stream stream) {
@@ -920,8 +1077,15 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
     scion_bvh b = bvhs[i];
     scion_trace_params p{};
     if (per_scene) p = per_scene[i];
-    if (!b || (n[i] > 0 && (!d_rays[i] || !d_hits[i])) || p.ordered_children > 3 || p.raster_width != 0 ||
+    if (!b || (n[i] > 0 && (!d_rays[i] || !d_hits[i])) || p.ordered_children > 3 || p.rays_per_fetch > 32 ||
         (reinterpret_cast<uintptr_t>(d_rays[i]) & 15u) || (reinterpret_cast<uintptr_t>(d_hits[i]) & 15u)) {
+      g_last_error = "scion_batch_create: scene " + std::to_string(i) + ": bad argument";
+      delete bt;
+      return SCION_ERR_INVALID_ARG;
+    }
+    if (p.raster_width != 0 || p.reg_stack != 0) {
+      g_last_error = "scion_batch_create: raster_width and reg_stack are plain-launch parameters (scene " +
+                     std::to_string(i) + ")";
       delete bt;
       return SCION_ERR_INVALID_ARG;
     }
@@ -954,11 +1118,11 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
     a.max_steps = p.max_steps ? p.max_steps : 2u * (b->n_nodes + b->n_leaf_entries) + 64u;
     a.ordered = order_mode(p.ordered_children);
     a.smem_stack = bt->smem_stack;
-    a.refill_min = 0;
+    a.refill_min = p.rays_per_fetch < 32 ? p.rays_per_fetch : 0u;
     a.status = b->d_scratch + 3;
     sc.begin = total;
     sc.family = (uint32_t)fam;
-    total += (n[i] + 31) / 32 * 32;
+    total += (n[i] + kBatchUnit - 1) / kBatchUnit * kBatchUnit;
     table.push_back(sc);
   }
   bt->n_scenes = (uint32_t)table.size();
@@ -975,10 +1139,18 @@ scion_status scion_batch_create(const scion_bvh *bvhs, const scion_ray *const *d
   if (e == cudaSuccess && !table.empty()) {
     const size_t smem = (size_t)bt->threads * bt->smem_stack * sizeof(uint2);
     int nb = 0;
+    int dev = current_device();
+    const scion_status so = ensure_smem_optin(batched_kernel_ptr(), smem, dev);
+    if (so != SCION_OK) {
+      if (bt->d_counters) cudaFree(bt->d_counters);
+      if (bt->d_scenes) cudaFree(bt->d_scenes);
+      delete bt;
+      return so;
+    }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel_ptr(), (int)bt->threads, smem);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const uint64_t want = ((uint64_t)total + bt->threads - 1) / bt->threads;
+    // one unit per warp at a time: more CTAs than units would only idle
+    const uint64_t per_cta = (uint64_t)kBatchUnit * (bt->threads / 32);
+    const uint64_t want = ((uint64_t)total + per_cta - 1) / per_cta;
     bt->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)std::max(nb, 1) * device_sms(dev), want));
   }
   if (e != cudaSuccess) {

@@ -9,8 +9,23 @@
 namespace scion {
 
 // Node families the batched kernel dispatches on (direct child references;
-// direct or indirect triangles).
-enum : uint32_t { kFamilyBin = 0, kFamilyW4F32 = 1, kFamilyW8F16 = 2, kFamilyW8U8 = 3 };
+// direct or indirect triangles): the width-2 own-box node with f32 or q16
+// boxes (AoS), 4-wide SoA nodes with f32, f16 or u8 boxes, 8-wide SoA f16,
+// 8-wide u8 AoS and SoA.
+enum : uint32_t {
+  kFamilyBin = 0,
+  kFamilyBinQ16 = 1,
+  kFamilyW4F32 = 2,
+  kFamilyW4F16 = 3,
+  kFamilyW4U8 = 4,
+  kFamilyW8F16 = 5,
+  kFamilyW8U8 = 6,
+  kFamilyW8U8S = 7
+};
+
+// Rays a warp takes per atomic from the global counter; every scene's range
+// in the global index space is padded to a multiple of it.
+constexpr uint32_t kBatchUnit = 32;
 
 struct alignas(16) BatchScene {
   TraceArgs a;               // the scene's trace arguments (rays, hits, BVH buffers)

@@ -14,12 +14,16 @@
 //      octrees, and k-d trees"); equal codes are ordered by their position;
 //   5. boxes bottom-up: a thread per leaf climbs while it is the second of
 //      the two children to arrive at a node (an atomic counter per node;
-//      nothing waits on another thread).
+//      nothing waits on another thread);
+//   6. leaf choice bottom-up in the same way: a subtree of at most leaf_max
+//      triangles becomes one leaf where the surface area heuristic prefers
+//      it to the subtree's best split.
 #include "lbvh.h"
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 namespace scion {
@@ -323,6 +327,46 @@ __global__ void boxes_kernel(int n, const uint32_t *__restrict__ ids, const floa
   }
 }
 
+// Surface area of node x in double (as the host's cost model computes it).
+__device__ __forceinline__ double node_area(const float *lo, const float *hi, uint32_t x) {
+  const double ex = (double)hi[3 * (size_t)x] - (double)lo[3 * (size_t)x];
+  const double ey = (double)hi[3 * (size_t)x + 1] - (double)lo[3 * (size_t)x + 1];
+  const double ez = (double)hi[3 * (size_t)x + 2] - (double)lo[3 * (size_t)x + 2];
+  return 2.0 * (ex * ey + ey * ez + ez * ex);
+}
+
+// 6. leaf choice bottom-up. A subtree covers a contiguous range of the
+//    sorted triangles, so it can become one leaf over that range. With node
+//    and triangle test cost 1 (as the host builder), cost(x) = min(area(x) *
+//    count(x) if count(x) <= leaf_max, area(x) + cost(left) + cost(right)),
+//    a radix leaf costing its area; whole[x] = 1 where the leaf is not
+//    dearer. The second child to arrive at a node computes it.
+__global__ void leaf_choice_kernel(int n, const uint32_t *__restrict__ left, const uint32_t *__restrict__ right,
+                                   const uint32_t *__restrict__ parent, const uint32_t *__restrict__ rlo,
+                                   const uint32_t *__restrict__ rhi, const float *__restrict__ nlo,
+                                   const float *__restrict__ nhi, uint32_t lmax, double *cost, uint8_t *whole,
+                                   uint32_t *arrived) {
+  const uint32_t first_leaf = (uint32_t)(n - 1);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    uint32_t p = parent[first_leaf + k];
+    while (p != kNone) {
+      __threadfence();
+      if (atomicAdd(arrived + p, 1u) == 0u) break;
+      const uint32_t l = left[p], r = right[p];
+      const double cl = l >= first_leaf ? node_area(nlo, nhi, l) : __ldcg(cost + l);
+      const double cr = r >= first_leaf ? node_area(nlo, nhi, r) : __ldcg(cost + r);
+      const double a = node_area(nlo, nhi, p);
+      const double split = a + cl + cr;
+      const uint32_t cnt = rhi[p] - rlo[p] + 1u;
+      const double leaf = cnt <= lmax ? a * (double)cnt : __longlong_as_double(0x7ff0000000000000ll);
+      const bool w = leaf <= split;
+      whole[p] = w ? 1 : 0;
+      cost[p] = w ? leaf : split;
+      p = parent[p];
+    }
+  }
+}
+
 // device allocations of one build, freed on every exit path
 struct Scratch {
   std::vector<void *> ptrs;
@@ -350,12 +394,15 @@ int grid_for(uint64_t n, int threads) {
 
 }  // namespace
 
-scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices, uint64_t n_tris,
-                        uint32_t leaf_max, cudaStream_t s, LogicalBVH *out, double *gpu_ms, std::string *err) {
+LbvhTree::~LbvhTree() {
+  for (void *p : owned) cudaFree(p);
+}
+
+scion_status lbvh_build_tree(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices, uint64_t n_tris,
+                             uint32_t leaf_max, cudaStream_t s, LbvhTree *out, std::string *err) {
   (void)n_verts;
-  out->nodes.clear();
-  out->prims.clear();
-  *gpu_ms = 0.0;
+  out->nv = 0;
+  out->gpu_ms = 0.0;
   if (n_tris == 0) return SCION_OK;
   const uint32_t n = (uint32_t)n_tris;
   const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
@@ -369,11 +416,19 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
     e = (call);                     \
     if (e != cudaSuccess) return fail(e, err); \
   } while (0)
+  // tree arrays: owned by the result
+  auto keep = [&](auto **p, size_t count) -> cudaError_t {
+    void *q = nullptr;
+    const cudaError_t r = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(**p));
+    if (r == cudaSuccess) out->owned.push_back(q);
+    *p = static_cast<std::remove_reference_t<decltype(*p)>>(q);
+    return r;
+  };
   SCION_LB(sc.get(&tlo, 3 * (size_t)n));
   SCION_LB(sc.get(&thi, 3 * (size_t)n));
   for (int b = 0; b < 2; ++b) {
-    SCION_LB(sc.get(&keys[b], npad));
-    SCION_LB(sc.get(&vals[b], npad));
+    SCION_LB(keep(&keys[b], npad));
+    SCION_LB(keep(&vals[b], npad));
   }
   SCION_LB(sc.get(&hist, (size_t)kRadix * tiles));
   SCION_LB(sc.get(&cb, 8));
@@ -410,6 +465,7 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
   uint32_t nv = 0;
   SCION_LB(cudaMemcpyAsync(&nv, nvalid, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   SCION_LB(cudaStreamSynchronize(s));
+  out->ids = vals[cur];
   if (nv == 0) {
     SCION_LB(cudaEventRecord(ev1, s));
     SCION_LB(cudaEventSynchronize(ev1));
@@ -417,19 +473,23 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
   }
   const size_t nn = 2 * (size_t)nv - 1;
   uint32_t *left, *right, *parent, *arrived, *rlo, *rhi;
-  uint8_t *axis;
+  uint8_t *axis, *whole;
   float *nlo, *nhi;
-  SCION_LB(sc.get(&left, nv));
-  SCION_LB(sc.get(&right, nv));
-  SCION_LB(sc.get(&rlo, nv));
-  SCION_LB(sc.get(&rhi, nv));
-  SCION_LB(sc.get(&axis, nv));
+  double *cost;
+  SCION_LB(keep(&left, nv));
+  SCION_LB(keep(&right, nv));
+  SCION_LB(keep(&rlo, nv));
+  SCION_LB(keep(&rhi, nv));
+  SCION_LB(keep(&axis, nv));
+  SCION_LB(keep(&whole, nv));
+  SCION_LB(keep(&nlo, 3 * nn));
+  SCION_LB(keep(&nhi, 3 * nn));
   SCION_LB(sc.get(&parent, nn));
   SCION_LB(sc.get(&arrived, nv));
-  SCION_LB(sc.get(&nlo, 3 * nn));
-  SCION_LB(sc.get(&nhi, 3 * nn));
+  SCION_LB(sc.get(&cost, nv));
   SCION_LB(cudaMemsetAsync(parent, 0xFF, nn * sizeof(uint32_t), s));
   SCION_LB(cudaMemsetAsync(arrived, 0, nv * sizeof(uint32_t), s));
+  SCION_LB(cudaMemsetAsync(whole, 0, nv, s));
   if (nv > 1) {
     radix_tree_kernel<<<grid_for(nv - 1, 256), 256, 0, s>>>(keys[cur], (int)nv, left, right, parent, axis, rlo,
                                                              rhi);
@@ -438,60 +498,55 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
   boxes_kernel<<<grid_for(nv, 256), 256, 0, s>>>((int)nv, vals[cur], tlo, thi, left, right, parent, nlo, nhi,
                                                   arrived);
   SCION_LB(cudaGetLastError());
+  const uint32_t lmax = leaf_max ? leaf_max : 1u;
+  if (nv > 1 && lmax > 1) {
+    SCION_LB(cudaMemsetAsync(arrived, 0, nv * sizeof(uint32_t), s));
+    leaf_choice_kernel<<<grid_for(nv, 256), 256, 0, s>>>((int)nv, left, right, parent, rlo, rhi, nlo, nhi, lmax,
+                                                          cost, whole, arrived);
+    SCION_LB(cudaGetLastError());
+  }
   SCION_LB(cudaEventRecord(ev1, s));
-  // download the tree
-  std::vector<uint32_t> hl(nv), hr(nv), ids(nv), hrl(nv), hrh(nv);
-  std::vector<uint8_t> hax(nv);
-  std::vector<float> hlo(3 * nn), hhi(3 * nn);
-  SCION_LB(cudaMemcpyAsync(ids.data(), vals[cur], nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  SCION_LB(cudaMemcpyAsync(hl.data(), left, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  SCION_LB(cudaMemcpyAsync(hr.data(), right, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  SCION_LB(cudaMemcpyAsync(hax.data(), axis, nv, cudaMemcpyDeviceToHost, s));
-  SCION_LB(cudaMemcpyAsync(hrl.data(), rlo, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  SCION_LB(cudaMemcpyAsync(hrh.data(), rhi, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  SCION_LB(cudaMemcpyAsync(hlo.data(), nlo, 3 * nn * sizeof(float), cudaMemcpyDeviceToHost, s));
-  SCION_LB(cudaMemcpyAsync(hhi.data(), nhi, 3 * nn * sizeof(float), cudaMemcpyDeviceToHost, s));
   SCION_LB(cudaStreamSynchronize(s));
   float ms = 0.f;
   SCION_LB(cudaEventElapsedTime(&ms, ev0, ev1));
-  *gpu_ms = ms;
+  out->gpu_ms = ms;
 #undef SCION_LB
-  // Leaves. A subtree covers a contiguous range of the sorted triangles, so
-  // it can become one leaf over that range. Bottom-up, each subtree of at
-  // most leaf_max triangles is kept whole when that is cheaper under the
-  // surface area heuristic than its best split (node and triangle test cost
-  // 1 each, as in the host builder): cost = min(area * count, area +
-  // cost(left) + cost(right)).
-  const uint32_t lmax = leaf_max ? leaf_max : 1u;
-  auto area_of = [&](uint32_t x) {
-    const double ex = (double)hhi[3 * (size_t)x] - hlo[3 * (size_t)x];
-    const double ey = (double)hhi[3 * (size_t)x + 1] - hlo[3 * (size_t)x + 1];
-    const double ez = (double)hhi[3 * (size_t)x + 2] - hlo[3 * (size_t)x + 2];
-    return 2.0 * (ex * ey + ey * ez + ez * ex);
-  };
-  std::vector<uint8_t> whole(nv > 1 ? nv - 1 : 0, 0);
-  if (nv > 1 && lmax > 1) {
-    std::vector<double> cost(nv - 1);
-    std::vector<uint32_t> pre, todo_c{0u};
-    pre.reserve(nv - 1);
-    while (!todo_c.empty()) {  // pre-order of the interior nodes
-      const uint32_t x = todo_c.back();
-      todo_c.pop_back();
-      pre.push_back(x);
-      if (hl[x] + 1 < nv) todo_c.push_back(hl[x]);
-      if (hr[x] + 1 < nv) todo_c.push_back(hr[x]);
-    }
-    auto cost_of = [&](uint32_t x) { return x + 1 < nv ? cost[x] : area_of(x); };
-    for (size_t i = pre.size(); i-- > 0;) {  // children before parents
-      const uint32_t x = pre[i];
-      const double a = area_of(x);
-      const double split = a + cost_of(hl[x]) + cost_of(hr[x]);
-      const uint32_t n = hrh[x] - hrl[x] + 1;
-      const double leaf = n <= lmax ? a * (double)n : INFINITY;
-      whole[x] = leaf <= split ? 1 : 0;
-      cost[x] = whole[x] ? leaf : split;
-    }
-  }
+  out->nv = nv;
+  out->left = left;
+  out->right = right;
+  out->rlo = rlo;
+  out->rhi = rhi;
+  out->axis = axis;
+  out->whole = whole;
+  out->nlo = nlo;
+  out->nhi = nhi;
+  return SCION_OK;
+}
+
+scion_status lbvh_download(const LbvhTree &t, cudaStream_t s, LogicalBVH *out, std::string *err) {
+  out->nodes.clear();
+  out->prims.clear();
+  const uint32_t nv = t.nv;
+  if (nv == 0) return SCION_OK;
+  const size_t nn = 2 * (size_t)nv - 1;
+  std::vector<uint32_t> hl(nv), hr(nv), ids(nv), hrl(nv), hrh(nv);
+  std::vector<uint8_t> hax(nv), whole(nv);
+  std::vector<float> hlo(3 * nn), hhi(3 * nn);
+  cudaError_t e = cudaSuccess;
+#define SCION_DL(dst, src, bytes) \
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s)
+  SCION_DL(ids.data(), t.ids, nv * sizeof(uint32_t));
+  SCION_DL(hl.data(), t.left, nv * sizeof(uint32_t));
+  SCION_DL(hr.data(), t.right, nv * sizeof(uint32_t));
+  SCION_DL(hax.data(), t.axis, nv);
+  SCION_DL(whole.data(), t.whole, nv);
+  SCION_DL(hrl.data(), t.rlo, nv * sizeof(uint32_t));
+  SCION_DL(hrh.data(), t.rhi, nv * sizeof(uint32_t));
+  SCION_DL(hlo.data(), t.nlo, 3 * nn * sizeof(float));
+  SCION_DL(hhi.data(), t.nhi, 3 * nn * sizeof(float));
+#undef SCION_DL
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e, err);
   // Logical tree, depth first from the root.
   out->prims = std::move(ids);
   out->nodes.reserve(nn);
@@ -534,6 +589,18 @@ scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *
     out->nodes[it.dst].right = r;
   }
   return SCION_OK;
+}
+
+scion_status lbvh_build(const float *d_verts, uint64_t n_verts, const uint32_t *d_indices, uint64_t n_tris,
+                        uint32_t leaf_max, cudaStream_t s, LogicalBVH *out, double *gpu_ms, std::string *err) {
+  out->nodes.clear();
+  out->prims.clear();
+  *gpu_ms = 0.0;
+  LbvhTree t;
+  scion_status st = lbvh_build_tree(d_verts, n_verts, d_indices, n_tris, leaf_max, s, &t, err);
+  if (st != SCION_OK) return st;
+  *gpu_ms = t.gpu_ms;
+  return lbvh_download(t, s, out, err);
 }
 
 }  // namespace scion

@@ -21,11 +21,10 @@ namespace scion {
 #define SCION_CPQ_GETTER SCION_CAT(SCION_CAT(SCION_CAT(cpq_kernels_w, SCION_W), _p), SCION_PREC)
 #endif
 
-// The register tier of the stack needs registers the 64-register cap of four
-// CTAs per SM does not leave (it would spill): three CTAs per SM for it.
+// The register tier of the stack spills under the 64-register cap of four
+// CTAs per SM; measured, that costs less than giving up a CTA per SM.
 template <int SOA, int CREF, bool ANY, bool STATS, int REG>
-__global__ void __launch_bounds__(kMaxThreadsPerBlock, REG > 0 && kMinBlocksPerSm > 3 ? 3 : kMinBlocksPerSm)
-    trace_kernel(TraceArgs a) {
+__global__ void __launch_bounds__(kMaxThreadsPerBlock, kMinBlocksPerSm) trace_kernel(TraceArgs a) {
   trace_kernel_body<SCION_FAMILY_OWN, SCION_W, SCION_PREC, SOA, CREF, ANY, STATS, REG>(a);
 }
 

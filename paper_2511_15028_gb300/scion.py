@@ -163,6 +163,11 @@ def lib():
         L.scion_debug_f16_round.restype = U32
         L.scion_debug_raster_slots.argtypes = [U64, U32]
         L.scion_debug_raster_slots.restype = U64
+        L.scion_debug_build_gpu_host_pack.argtypes = [P, U64, P, U64, ctypes.POINTER(LayoutDesc), P,
+                                                      ctypes.POINTER(P)]
+        L.scion_debug_build_gpu_host_pack.restype = I
+        L.scion_debug_bvh_bytes.argtypes = [P, P, U64, P, U64, P, U64, P]
+        L.scion_debug_bvh_bytes.restype = I
         L.scion_debug_read_bandwidth.argtypes = [P, U64, U32, P, P]
         L.scion_debug_read_bandwidth.restype = I
         L.scion_debug_f16_decode.argtypes = [U32]
@@ -246,11 +251,12 @@ def scion_build(verts, desc: LayoutDesc, indices=None, stream=None) -> BVH:
     return BVH(h, nt, nv, desc)
 
 
-def scion_build_gpu(verts, desc: LayoutDesc, indices=None, stream=None) -> BVH:
-    """Build with the logical BVH2 constructed on the GPU (linear BVH, one
-    triangle per leaf), then packed into `desc`. verts: float32 [n_verts, 3]
-    and indices: int32/uint32 [n_tris, 3] (or None for a soup), CUDA tensors
-    or numpy arrays (copied to the device first)."""
+def scion_build_gpu(verts, desc: LayoutDesc, indices=None, stream=None, host_pack: bool = False) -> BVH:
+    """Build with the logical BVH2 constructed on the GPU (linear BVH) and
+    packed into `desc` on the GPU (host_pack=True: by the host packers, the
+    debug reference). verts: float32 [n_verts, 3] and indices: int32/uint32
+    [n_tris, 3] (or None for a soup), CUDA tensors or numpy arrays (copied to
+    the device first)."""
     import torch
     v = torch.as_tensor(verts, dtype=torch.float32).cuda().contiguous()
     ix = None
@@ -263,10 +269,21 @@ def scion_build_gpu(verts, desc: LayoutDesc, indices=None, stream=None) -> BVH:
     nv = v.shape[0]
     nt = nv // 3 if ix is None else ix.shape[0]
     h = ctypes.c_void_p()
-    _check(lib().scion_build_gpu(ctypes.c_void_p(v.data_ptr()), nv,
-                                 None if ix is None else ctypes.c_void_p(ix.data_ptr()), nt,
-                                 ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(h)), "scion_build_gpu")
+    fn = lib().scion_debug_build_gpu_host_pack if host_pack else lib().scion_build_gpu
+    _check(fn(ctypes.c_void_p(v.data_ptr()), nv, None if ix is None else ctypes.c_void_p(ix.data_ptr()), nt,
+              ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(h)), "scion_build_gpu")
     return BVH(h, nt, nv, desc)
+
+
+def scion_debug_bvh_bytes(bvh: BVH):
+    """(nodes, nodes2, prims) byte arrays copied from a BVH's device buffers."""
+    sizes = (ctypes.c_uint64 * 3)()
+    _check(lib().scion_debug_bvh_bytes(bvh.handle, None, 0, None, 0, None, 0, sizes), "scion_debug_bvh_bytes")
+    bufs = [np.zeros(max(int(n), 1), np.uint8) for n in sizes]
+    P = lambda x: x.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().scion_debug_bvh_bytes(bvh.handle, P(bufs[0]), bufs[0].size, P(bufs[1]), bufs[1].size,
+                                       P(bufs[2]), bufs[2].size, sizes), "scion_debug_bvh_bytes")
+    return tuple(b[:int(n)] for b, n in zip(bufs, sizes))
 
 
 def scion_refit(bvh: BVH, verts, stream=None) -> None:

@@ -161,3 +161,35 @@ def test_config4_full_size(mods, oracle_mod):
         got = scion.split_hits(batch.hits[i])[pick]
         assert got.tobytes() == exp.tobytes(), f"scene {i} ({sc.name}, {chosen[i].name}) vs oracle"
         assert scion.scion_get_status(bvhs[i]) == 0
+
+
+def test_batched_every_family_and_fetch_mode(mods, oracle_mod):
+    """Every node family of the batched kernel, with direct and indirect
+    triangles, under warp batches and warp refill at several thresholds and
+    child orders, in one launch: hits equal the oracle's."""
+    scion, _ = mods
+    fams = [dict(), dict(box_prec="q16"), dict(width=4, box_layout="soa"), dict(width=4, box_layout="soa", box_prec="f16"),
+            dict(width=4, box_layout="soa", box_prec="u8", order="bfs"), dict(width=8, box_layout="soa", box_prec="f16"),
+            dict(width=8, box_prec="u8"), dict(width=8, box_layout="soa", box_prec="u8", order="treelet")]
+    modes = [{}, dict(rays_per_fetch=1), dict(rays_per_fetch=8, ordered_children=2),
+             dict(rays_per_fetch=31, ordered_children=3), dict(ordered_children=2)]
+    wl = scenes.config4_workload(seed=79, n_scenes=16, scale=0.01)
+    bvhs, rays, params = [], [], []
+    for i, (sc, r) in enumerate(wl):
+        kw = dict(fams[i % len(fams)], prim_ref="direct" if i < 8 else "indirect")
+        bvhs.append(scion.scion_build(sc.verts, scion.layout(**kw), sc.indices))
+        rays.append(torch.from_numpy(r).cuda())
+        params.append(modes[i % len(modes)])
+    batch = scion.Batch(bvhs, rays, params=params)
+    assert batch.info() == {"batched_scenes": 16, "plain_scenes": 0}
+    for _ in range(2):  # the counters reset themselves between launches
+        for h in batch.hits:
+            h.fill_(-1)
+        hits = batch.launch()
+        torch.cuda.synchronize()
+        for i, (sc, r) in enumerate(wl):
+            exp = oracle_mod.BVH2(sc.triangles()).closest(r)
+            assert scion.split_hits(hits[i]).tobytes() == exp.tobytes(), (i, params[i])
+            assert scion.scion_get_status(bvhs[i]) == 0
+    with pytest.raises(scion.ScionError):  # register stack tiers are for plain launches
+        scion.Batch(bvhs[:1], rays[:1], params=[dict(reg_stack=4)])

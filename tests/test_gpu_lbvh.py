@@ -139,3 +139,67 @@ def test_invalid_arguments(sc_mod):
         sc_mod.scion_build_gpu(torch.from_numpy(base).cuda(), d, np.array([[0, 1, 7]], np.uint32))
     with pytest.raises(sc_mod.ScionError):
         sc_mod.scion_build_gpu(torch.from_numpy(base).cuda(), sc_mod.layout(box_prec="q16", leaf_max=16))
+
+
+def _same_bytes(scion, a, b, what):
+    ia, ib = scion.scion_bvh_info(a), scion.scion_bvh_info(b)
+    assert ia == ib, f"{what}: info {ia} vs {ib}"
+    for name, x, y in zip(("nodes", "nodes2", "prims"), scion.scion_debug_bvh_bytes(a), scion.scion_debug_bvh_bytes(b)):
+        assert x.size == y.size, f"{what}: {name} sizes {x.size} vs {y.size}"
+        bad = np.flatnonzero(x != y)
+        assert bad.size == 0, f"{what}: {name} differ at {bad.size} bytes, first {bad[:8]}"
+
+
+def test_gpu_packer_bytes_equal_host_packer(sc_mod):
+    """The GPU packer writes the same bytes as the host packers for the same
+    GPU-built logical tree, on every layout of the test sweep (the treelet
+    order and the shared slab are packed on the host by both calls), on an
+    indexed height field and on a soup with ties and non-finite triangles."""
+    from layout_cases import all_layouts
+    scion = sc_mod
+    sc = scenes.config1_scene()
+    rng = scenes.rng_for(51)
+    soup = scenes.random_soup(rng, 3000, mu=math.log(0.05))
+    soup[30:33] = soup[0:3]                    # a duplicate triangle: equal Morton codes
+    soup[100, 1] = np.nan                      # left out of the tree
+    inputs = [(torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.indices.astype(np.int32)).cuda()),
+              (torch.from_numpy(soup).cuda(), None)]
+    for kw in all_layouts():
+        for leaf_max in (4, 1):
+            desc = scion.layout(leaf_max=leaf_max, **kw)
+            for v, ix in inputs:
+                try:
+                    ref = scion.scion_build_gpu(v, desc, ix, host_pack=True)
+                except scion.ScionError as e:  # the layout cannot hold this tree: both must refuse alike
+                    with pytest.raises(scion.ScionError) as e2:
+                        scion.scion_build_gpu(v, desc, ix)
+                    assert e2.value.status == e.status, kw
+                    continue
+                got = scion.scion_build_gpu(v, desc, ix)
+                _same_bytes(scion, got, ref, f"{kw} leaf_max={leaf_max} indexed={ix is not None}")
+
+
+def test_gpu_packer_full_size(sc_mod, oracle_mod):
+    """2^23 random triangles: the GPU packer's bytes equal the host packer's
+    for the layouts the benchmark sweeps in both orders and one of each
+    own-box codec, and it is much faster than packing on the host."""
+    import time
+    scion = sc_mod
+    sc = scenes.config3_scene()
+    dv = torch.from_numpy(sc.verts).cuda()
+    for kw in (dict(width=4, box_layout="soa", box_prec="u8", order="bfs", prim_ref="direct"),
+               dict(width=4, box_layout="soa", prim_ref="direct"), dict(width=8, box_prec="u8"),
+               dict(width=8, box_layout="soa", box_prec="f16", child_ref="indirect", order="bfs"),
+               dict(box_prec="q16", box_layout="soa"), dict(prim_ref="direct"),
+               dict(box_prec="eq10", child_ref="indirect", order="bfs")):
+        desc = scion.layout(**kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = scion.scion_build_gpu(dv, desc)
+        t_gpu = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ref = scion.scion_build_gpu(dv, desc, host_pack=True)
+        t_host = time.perf_counter() - t0
+        _same_bytes(scion, got, ref, str(kw))
+        assert t_gpu < t_host, (kw, t_gpu, t_host)
+        del got, ref
