@@ -458,10 +458,11 @@ def pareto(points):
     return sorted(front, key=lambda n: points[n][0])
 
 
-def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
+def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None, fixed=None):
     """2^23 random triangles and 2^23 random rays in the unit cube (BVH far
     larger than L2): closest hit (tmax inf) and any hit (tmax 0.05) for every
-    swept layout, built from one logical BVH."""
+    swept layout, built from one logical BVH. fixed = (closest mode, any
+    mode) skips the per-layout trials (to profile exactly those launches)."""
     from paper_2511_15028_gb300 import scenes
     t0 = time.time()
     sc = scenes.config3_scene()
@@ -490,7 +491,10 @@ def bench_incoherent(scion, torch, steps, warmup, hbm_peak, only=None):
         res = {}
         for q, fn, r, o in (("closest", scion.scion_trace_closest, rays, hits),
                             ("any", scion.scion_trace_any, short, occ)):
-            mode, trials = pick_fetch(scion, torch, bvh, fn, r, o, reps=2)
+            if fixed:
+                mode, trials = fixed[0 if q == "closest" else 1], {}
+            else:
+                mode, trials = pick_fetch(scion, torch, bvh, fn, r, o, reps=2)
             p = FETCH_MODES[mode] or None
             for _ in range(warmup):
                 fn(bvh, r, o, params=p)
@@ -864,8 +868,9 @@ def main():
     ap.add_argument("--layouts", default="all", help="all | comma-separated sweep names")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fetch", default=None,
-                    help="primary,bounce,shadow fetch modes (names of FETCH_MODES / RASTER_MODES); skips the "
-                         "per-layout trials, e.g. to profile exactly the modes a plain run chose")
+                    help="primary,bounce,shadow fetch modes (names of FETCH_MODES / RASTER_MODES), or with "
+                         "--section incoherent closest,any; skips the per-layout trials, e.g. to profile "
+                         "exactly the modes a plain run chose")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the incoherent, batched, backward, build and closest point sections")
     ap.add_argument("--section", default="all", choices=("all",) + SECTIONS,
@@ -899,7 +904,8 @@ def main():
     if args.section != "all":
         only = None if args.layouts == "all" else args.layouts.split(",")
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        fns = {"incoherent": lambda: bench_incoherent(scion, torch, args.steps, args.warmup, hbm_peak, only),
+        fixed = args.fetch.split(",") if args.fetch else None
+        fns = {"incoherent": lambda: bench_incoherent(scion, torch, args.steps, args.warmup, hbm_peak, only, fixed),
                "batched": lambda: bench_batched(scion, torch, args.steps, args.warmup, flush),
                "backward": lambda: bench_backward(scion, torch, args.steps, args.warmup, flush),
                "build": lambda: bench_build(scion, torch, args.steps, args.warmup),

@@ -335,10 +335,11 @@ scion_status scion_trace_stats(scion_bvh bvh, const scion_ray *d_rays, uint64_t 
                                uint64_t *d_counters);
 
 /* Closest hit for callers that cannot allocate device memory when they
- * trace — for example code running while a CUDA graph is captured in global
- * capture mode, where cudaMalloc is not permitted, or an application that
- * gives all device memory to its own arena and forbids later allocations.
- * The paper has no counterpart; this is a property of this library only.
+ * trace: an application that hands all device memory to its own arena up
+ * front and forbids any later allocation, or a latency-bound thread that must
+ * not enter the driver's allocator (cudaMalloc can synchronize the device and
+ * take milliseconds). The paper has no counterpart; this is a property of
+ * this library only.
  *
  * Same arguments and results as scion_trace_closest (the BVH, rays and hits
  * are the caller's, built and allocated beforehand). The traversal's work

@@ -1341,10 +1341,10 @@ float scion_debug_f16_decode(uint32_t h) { return f16_to_f32((uint16_t)h); }
 }  // extern "C"
 
 // ---------------------------------------------------------------- allocation-free closest hit
-// Some callers must not allocate device memory while they trace: code that runs
-// while a CUDA graph is being captured in global capture mode (where
-// cudaMalloc is not permitted), or a host application that hands all device
-// memory to its own arena up front and forbids any later allocation.
+// Some callers must not allocate device memory while they trace: a host
+// application that hands all device memory to its own arena up front and
+// forbids any later allocation, or a latency-bound thread that must not enter
+// the driver's allocator (cudaMalloc can synchronize the device).
 // scion_trace_closest_noalloc serves them: the traversal's per-launch work
 // counters live in the fixed array below, reserved once when the library's
 // device code is loaded, instead of in memory that scion_build allocated with

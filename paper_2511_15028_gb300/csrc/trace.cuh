@@ -140,25 +140,57 @@ __device__ __forceinline__ bool slab_t(const Ray &r, float t0x, float t0y, float
   return a <= b;
 }
 
-// The same for a box given by its corners: near/far planes by direction sign,
-// distance = fma(plane, 1/d, -o/d).
+// Two fused multiply-adds with one instruction (fma.rn.f32x2, sm_100 and
+// later): the same IEEE fma rounding per element as two fmaf calls.
+__device__ __forceinline__ void fma_pair(float a0, float a1, float m, float b, float &r0, float &r1) {
+  const float2 r = __ffma2_rn(make_float2(a0, a1), make_float2(m, m), make_float2(b, b));
+  r0 = r.x;
+  r1 = r.y;
+}
+// Two exact small-integer decodes x - 2^23 (the code sits in the low
+// mantissa bits of 2^23) with one add.f32x2.
+__device__ __forceinline__ void unbias_pair(float x0, float x1, float &r0, float &r1) {
+  const float2 r = __fadd2_rn(make_float2(x0, x1), make_float2(-8388608.0f, -8388608.0f));
+  r0 = r.x;
+  r1 = r.y;
+}
+
+// The six plane distances of a box given by its corners: near/far planes by
+// direction sign, distance = fma(plane, 1/d, -o/d), each axis's near and far
+// plane in one paired fma.
+__device__ __forceinline__ void box_planes(const Ray &r, float lox, float loy, float loz, float hix, float hiy,
+                                           float hiz, float (&t0)[3], float (&t1)[3]) {
+  fma_pair(r.nx ? hix : lox, r.nx ? lox : hix, r.rx, -r.orx, t0[0], t1[0]);
+  fma_pair(r.ny ? hiy : loy, r.ny ? loy : hiy, r.ry, -r.ory, t0[1], t1[1]);
+  fma_pair(r.nz ? hiz : loz, r.nz ? loz : hiz, r.rz, -r.orz, t0[2], t1[2]);
+}
+
+// The slab test of a box given by its corners. PAIRED = false takes one fmaf
+// per plane: a paired fma wants each ray constant twice in a register pair,
+// which makes the 64-register wide-node kernels spill.
+template <bool PAIRED = true>
 __device__ __forceinline__ bool slab(const Ray &r, float lox, float loy, float loz, float hix,
                                      float hiy, float hiz, float tlim, float &tn) {
-  const float nx = r.nx ? hix : lox, fx = r.nx ? lox : hix;
-  const float ny = r.ny ? hiy : loy, fy = r.ny ? loy : hiy;
-  const float nz = r.nz ? hiz : loz, fz = r.nz ? loz : hiz;
-  return slab_t(r, fmaf(nx, r.rx, -r.orx), fmaf(ny, r.ry, -r.ory), fmaf(nz, r.rz, -r.orz),
-                fmaf(fx, r.rx, -r.orx), fmaf(fy, r.ry, -r.ory), fmaf(fz, r.rz, -r.orz), tlim, tn);
+  float t0[3], t1[3];
+  if (PAIRED) {
+    box_planes(r, lox, loy, loz, hix, hiy, hiz, t0, t1);
+  } else {
+    const float nx = r.nx ? hix : lox, fx = r.nx ? lox : hix;
+    const float ny = r.ny ? hiy : loy, fy = r.ny ? loy : hiy;
+    const float nz = r.nz ? hiz : loz, fz = r.nz ? loz : hiz;
+    t0[0] = fmaf(nx, r.rx, -r.orx); t0[1] = fmaf(ny, r.ry, -r.ory); t0[2] = fmaf(nz, r.rz, -r.orz);
+    t1[0] = fmaf(fx, r.rx, -r.orx); t1[1] = fmaf(fy, r.ry, -r.ory); t1[2] = fmaf(fz, r.rz, -r.orz);
+  }
+  return slab_t(r, t0[0], t0[1], t0[2], t1[0], t1[1], t1[2], tlim, tn);
 }
 
 // The conservative ray interval [tn, tf] of a box, clamped to [tmin, tlim].
 __device__ __forceinline__ bool slab_interval(const Ray &r, float lox, float loy, float loz, float hix,
                                               float hiy, float hiz, float tlim, float &tn, float &tf) {
-  const float nx = r.nx ? hix : lox, fx = r.nx ? lox : hix;
-  const float ny = r.ny ? hiy : loy, fy = r.ny ? loy : hiy;
-  const float nz = r.nz ? hiz : loz, fz = r.nz ? loz : hiz;
-  tn = fmaxf(fmax3(fmaf(nx, r.rx, -r.orx), fmaf(ny, r.ry, -r.ory), fmaf(nz, r.rz, -r.orz)) * kNearScale, r.tmin);
-  tf = fminf(fmin3(fmaf(fx, r.rx, -r.orx), fmaf(fy, r.ry, -r.ory), fmaf(fz, r.rz, -r.orz)) * kFarScale, tlim);
+  float t0[3], t1[3];
+  box_planes(r, lox, loy, loz, hix, hiy, hiz, t0, t1);
+  tn = fmaxf(fmax3(t0[0], t0[1], t0[2]) * kNearScale, r.tmin);
+  tf = fminf(fmin3(t1[0], t1[1], t1[2]) * kFarScale, tlim);
   return tn <= tf;
 }
 
@@ -447,12 +479,15 @@ struct WideNode {
   // permute puts the code into the low mantissa bits of 2^23, then 2^23 is
   // taken off (full-rate integer/float ops instead of an integer-to-float
   // conversion)
-  static __device__ __forceinline__ float code(const uint4 (&q)[NQ], int k, int c) {
+  static __device__ __forceinline__ float code_biased(const uint4 (&q)[NQ], int k, int c) {
     const int off = box_off(k, c);
     const uint32_t w = qword(q, off >> 2);
     const uint32_t b = (uint32_t)(off & 3);
     const uint32_t sel = kElem == 1 ? (0x7540u | b) : (0x7400u | ((b + 1u) << 4) | b);
-    return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.0f;
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, sel));  // 2^23 + code
+  }
+  static __device__ __forceinline__ float code(const uint4 (&q)[NQ], int k, int c) {
+    return code_biased(q, k, c) - 8388608.0f;
   }
 };
 
@@ -537,6 +572,9 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Co
       bz = fmaf(__uint_as_float(q[0].z), r.rz, -r.orz);
     }
     const float tlim = ANY ? r.tmax : fminf(r.tmax, L.b.t);
+    // paired decode and fma (f32x2) for the grid codes; the 8-wide kernels
+    // would spill with the extra register pairs
+    constexpr bool kPaired = W <= 4;
     uint32_t cref[W];
     float ctn[W];
     uint32_t base_node = 0, base_prim = 0, leaf_acc = 0;
@@ -578,11 +616,17 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Co
             const float rc = c == 0 ? r.rx : (c == 1 ? r.ry : r.rz), oc = c == 0 ? r.orx : (c == 1 ? r.ory : r.orz);
             if (N::kGrid) {
               const uint32_t sel = N::kElem == 1 ? (0x7540u | b) : (0x7400u | ((b + 1u) << 4) | b);
-              const float nq = __uint_as_float(__byte_perm(nw[c], 0x4B000000u, sel)) - 8388608.0f;
-              const float fq = __uint_as_float(__byte_perm(fw[c], 0x4B000000u, sel)) - 8388608.0f;
+              const float nb = __uint_as_float(__byte_perm(nw[c], 0x4B000000u, sel));
+              const float fb = __uint_as_float(__byte_perm(fw[c], 0x4B000000u, sel));
               const float ac = c == 0 ? ax : (c == 1 ? ay : az), bc = c == 0 ? bx : (c == 1 ? by : bz);
-              t0[c] = fmaf(nq, ac, bc);
-              t1[c] = fmaf(fq, ac, bc);
+              if (kPaired) {
+                float nq, fq;
+                unbias_pair(nb, fb, nq, fq);
+                fma_pair(nq, fq, ac, bc, t0[c], t1[c]);
+              } else {
+                t0[c] = fmaf(nb - 8388608.0f, ac, bc);
+                t1[c] = fmaf(fb - 8388608.0f, ac, bc);
+              }
             } else {
               const float nv = __half2float(__ushort_as_half((unsigned short)((nw[c] >> (b * 8)) & 0xFFFFu)));
               const float fv = __half2float(__ushort_as_half((unsigned short)((fw[c] >> (b * 8)) & 0xFFFFu)));
@@ -604,13 +648,24 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Co
       float tn;
       bool hit;
       if (N::kGrid) {
-        const float lx = N::code(q, k, 0), ly = N::code(q, k, 1), lz = N::code(q, k, 2);
-        const float hx = N::code(q, k, 3), hy = N::code(q, k, 4), hz = N::code(q, k, 5);
-        const float nqx = r.nx ? hx : lx, fqx = r.nx ? lx : hx;
-        const float nqy = r.ny ? hy : ly, fqy = r.ny ? ly : hy;
-        const float nqz = r.nz ? hz : lz, fqz = r.nz ? lz : hz;
-        hit = slab_t(r, fmaf(nqx, ax, bx), fmaf(nqy, ay, by), fmaf(nqz, az, bz), fmaf(fqx, ax, bx),
-                     fmaf(fqy, ay, by), fmaf(fqz, az, bz), tlim, tn);
+        // per axis: near and far code of the child (decoded in one paired
+        // add), then both plane distances in one paired fma
+        float t0[3], t1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const bool neg = c == 0 ? r.nx : (c == 1 ? r.ny : r.nz);
+          const float lb = N::code_biased(q, k, c), hb = N::code_biased(q, k, c + 3);
+          const float ac = c == 0 ? ax : (c == 1 ? ay : az), bc = c == 0 ? bx : (c == 1 ? by : bz);
+          if (kPaired) {
+            float nq, fq;
+            unbias_pair(neg ? hb : lb, neg ? lb : hb, nq, fq);
+            fma_pair(nq, fq, ac, bc, t0[c], t1[c]);
+          } else {
+            t0[c] = fmaf((neg ? hb : lb) - 8388608.0f, ac, bc);
+            t1[c] = fmaf((neg ? lb : hb) - 8388608.0f, ac, bc);
+          }
+        }
+        hit = slab_t(r, t0[0], t0[1], t0[2], t1[0], t1[1], t1[2], tlim, tn);
       } else {
         float lo[3], hi[3];
 #pragma unroll
@@ -624,7 +679,7 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Co
             hi[c] = __half2float(__ushort_as_half((unsigned short)qh));
           }
         }
-        hit = slab(r, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], tlim, tn);
+        hit = slab<false>(r, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], tlim, tn);
       }
       hit = hit && ref != kEmptyRef;
       cref[k] = hit ? ref : kEmptyRef;
@@ -664,9 +719,21 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Co
     }
     L.cur = next != kEmptyRef ? next : pop_next<ANY>(st, L.b.t);
   } else {
-    if (visit_leaf<ANY, STATS>(a, r, ref_leaf_first(cur), ref_leaf_count(cur), L.b, cnt)) {
+    // Nodes up to 4 wide take one triangle per step: the entry then names the
+    // leaf's remaining triangles (first + 1, count - 1), so a lane in a leaf
+    // holds its warp for one triangle test per step rather than for the whole
+    // leaf while the other lanes wait. 8-wide nodes (measured slower that way
+    // on coherent rays) and the counting kernels test the whole leaf at once
+    // (the same triangles, so the same counts).
+    const uint32_t count = ref_leaf_count(cur);
+    constexpr bool kWhole = STATS || W > 4;
+    if (visit_leaf<ANY, STATS>(a, r, ref_leaf_first(cur), kWhole ? count : 1u, L.b, cnt)) {
       L.found = true;
       L.cur = kEmptyRef;
+      return;
+    }
+    if (!kWhole && count > 1u) {
+      L.cur = cur + (1u << 5) - (1u << 1);  // ref_leaf(first + 1, count - 1)
       return;
     }
     L.cur = pop_next<ANY>(st, L.b.t);
@@ -675,12 +742,14 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Co
 
 // Exact small-integer to float conversions with full-rate integer ops: the
 // code goes into the low mantissa bits of 2^23, then 2^23 is subtracted.
-__device__ __forceinline__ float u16lo_f(uint32_t w) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7410u)) - 8388608.0f;
+__device__ __forceinline__ float u16lo_b(uint32_t w) {  // 2^23 + low half
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7410u));
 }
-__device__ __forceinline__ float u16hi_f(uint32_t w) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7432u)) - 8388608.0f;
+__device__ __forceinline__ float u16hi_b(uint32_t w) {  // 2^23 + high half
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7432u));
 }
+__device__ __forceinline__ float u16lo_f(uint32_t w) { return u16lo_b(w) - 8388608.0f; }
+__device__ __forceinline__ float u16hi_f(uint32_t w) { return u16hi_b(w) - 8388608.0f; }
 __device__ __forceinline__ float eq10_f(uint32_t w, int axis) {
   return __uint_as_float(0x4B000000u | eq10_code(w, axis)) - 8388608.0f;
 }
@@ -732,12 +801,14 @@ __device__ __forceinline__ void step_bin(const TraceArgs &a, Lane &L, S &st, Cou
     if (PREC == PREC_Q16) {
       // codes: w0 = lo.x | lo.y << 16, w1 = lo.z | hi.x << 16, w2 = hi.y | hi.z << 16
       word = SOA ? __ldg(reinterpret_cast<const uint32_t *>(a.nodes2) + cur) : w3;
-      lo0 = fmaf(u16lo_f(w0), a.frame[3], a.frame[0]);
-      lo1 = fmaf(u16hi_f(w0), a.frame[4], a.frame[1]);
-      lo2 = fmaf(u16lo_f(w1), a.frame[5], a.frame[2]);
-      hi0 = fmaf(u16hi_f(w1), a.frame[3], a.frame[0]);
-      hi1 = fmaf(u16lo_f(w2), a.frame[4], a.frame[1]);
-      hi2 = fmaf(u16hi_f(w2), a.frame[5], a.frame[2]);
+      // per axis the lo and hi code decoded, then placed on the grid, in pairs
+      float c0l, c0h, c1l, c1h, c2l, c2h;
+      unbias_pair(u16lo_b(w0), u16hi_b(w1), c0l, c0h);
+      unbias_pair(u16hi_b(w0), u16lo_b(w2), c1l, c1h);
+      unbias_pair(u16lo_b(w1), u16hi_b(w2), c2l, c2h);
+      fma_pair(c0l, c0h, a.frame[3], a.frame[0], lo0, hi0);
+      fma_pair(c1l, c1h, a.frame[4], a.frame[1], lo1, hi1);
+      fma_pair(c2l, c2h, a.frame[5], a.frame[2], lo2, hi2);
     } else {
       // w0 = lo codes counted up from wlo, w1 = hi codes counted down from whi
       word = w2;

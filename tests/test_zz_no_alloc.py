@@ -1,6 +1,7 @@
 """scion_trace_closest_noalloc: the closest-hit entry point for callers that
-cannot allocate device memory while tracing (e.g. under a CUDA graph capture
-in global mode, or inside an application whose arena owns all device memory).
+cannot allocate device memory while tracing (an application whose arena owns
+all device memory, or a latency-bound thread that must stay out of the
+driver's allocator).
 
 Called through the C ABI; its hits must equal scion_trace_closest's on two
 calls in a row (both share the library's static scratch array). Kept in a file
