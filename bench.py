@@ -830,6 +830,45 @@ def bench_backward(scion, torch, steps, warmup, flush_buf=None):
     return out
 
 
+# ------------------------------------------------------------------ host cost per call
+def bench_host(scion, torch, calls=1000, n=1024):
+    """Host time per trace call: `calls` back-to-back scion_trace_closest
+    calls of n rays (config-1 scene, BVH4), through the C ABI directly
+    (ctypes, arguments prepared once) and through the Python binding, timed
+    with a host clock; the GPU time of the same loop (CUDA events) is given
+    beside it, since a loop faster on the host than on the GPU measures the
+    GPU once the launch queue is full."""
+    import ctypes
+
+    from paper_2511_15028_gb300 import scenes
+    sc = scenes.config1_scene()
+    bvh = scion.scion_build(sc.verts, scion.layout(width=4, box_layout="soa", prim_ref="direct"), sc.indices)
+    rays = torch.from_numpy(scenes.config1_rays()[:n]).cuda()
+    hits = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    L = scion.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = (bvh.handle, ctypes.c_void_p(rays.data_ptr()), ctypes.c_uint64(n), ctypes.c_void_p(hits.data_ptr()),
+            None, stream)
+    out = {"calls": calls, "rays_per_call": n}
+    for name, fn in (("c_abi", lambda: L.scion_trace_closest(*args)),
+                     ("python", lambda: scion.scion_trace_closest(bvh, rays, hits))):
+        for _ in range(50):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            fn()
+        t1 = time.perf_counter()
+        b.record()
+        b.synchronize()
+        out[f"{name}_host_us_per_call"] = round((t1 - t0) / calls * 1e6, 2)
+        out[f"{name}_gpu_us_per_call"] = round(a.elapsed_time(b) / calls * 1e3, 2)
+    scion.scion_destroy(bvh)
+    return out
+
+
 # ------------------------------------------------------------------ main
 def _peaks():
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -856,7 +895,7 @@ def run_section(rank, name, fn, *a, **kw):
     return res
 
 
-SECTIONS = ("incoherent", "batched", "backward", "build", "cpq", "l2")
+SECTIONS = ("incoherent", "batched", "backward", "build", "cpq", "l2", "host")
 
 
 def main():
@@ -910,7 +949,8 @@ def main():
                "backward": lambda: bench_backward(scion, torch, args.steps, args.warmup, flush),
                "build": lambda: bench_build(scion, torch, args.steps, args.warmup),
                "cpq": lambda: bench_cpq(scion, torch, args.steps, args.warmup, hbm_peak),
-               "l2": lambda: measure_l2_peak(scion, torch)}
+               "l2": lambda: measure_l2_peak(scion, torch),
+               "host": lambda: bench_host(scion, torch)}
         res = fns[args.section]()
         emit(rank, {"section": args.section, "steps": args.steps, "warmup": args.warmup, **res})
         return
@@ -1032,6 +1072,7 @@ def main():
         run_section(rank, "backward", bench_backward, scion, torch, args.steps, args.warmup, flush_buf)
         run_section(rank, "build", bench_build, scion, torch, args.steps, args.warmup)
         run_section(rank, "closest_point", bench_cpq, scion, torch, args.steps, args.warmup, hbm_peak)
+        run_section(rank, "host", bench_host, scion, torch)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -1055,7 +1096,7 @@ def main():
         "bvh_mb": round(r["bvh_mb"], 2),
         "per_query_ms": {k: round(v, 4) for k, v in r["per_query_ms"].items()},
         "sections": "earlier JSON lines: l2_peak, coherent_layouts (every layout, Pareto front)"
-                    + ("" if args.no_extra else ", incoherent, batched, backward, build, closest_point"),
+                    + ("" if args.no_extra else ", incoherent, batched, backward, build, closest_point, host"),
     }
     emit(rank, line)
     if dist is not None:

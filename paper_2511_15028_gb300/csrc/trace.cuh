@@ -934,10 +934,14 @@ __device__ __forceinline__ void start_ray(const TraceArgs &a, Lane &L) {
 }
 
 // The ring pays for its extra register where the kernel has room: the own-box
-// bvh2 kernels (all but the shared slab) and the any-hit kernels of nodes up to
-// 4 wide; in the other 64-register kernels it would spill.
+// bvh2 kernels (all but the shared slab), the any-hit kernels of nodes up to 4
+// wide and the closest-hit kernels of 2/4-wide nodes with f16 or u8 boxes; in
+// the other 64-register kernels it would spill.
 template <bool OWN, int PREC, int W, bool ANY, int REG>
-using StackFor = StackT<OWN && PREC == PREC_SLAB, (OWN && PREC != PREC_SLAB) || (!OWN && ANY && W <= 4), REG>;
+using StackFor = StackT<OWN && PREC == PREC_SLAB,
+                        (OWN && PREC != PREC_SLAB) ||
+                            (!OWN && W <= 4 && (ANY || PREC == PREC_F16 || PREC == PREC_U8)),
+                        REG>;
 
 // ------------------------------------------------------------------ kernel body
 // Trace one ray to completion with the layout's step function.

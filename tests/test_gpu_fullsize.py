@@ -5,7 +5,7 @@ the incoherent 2^23-triangle soup with 2^23 random rays (closest hit and
 any hit with tmax 0.05). Config-2 outputs are all compared with the CPU
 oracle's BVH2 (bounce and shadow rays come from its own primary hits);
 config-3 outputs too (all 2^23 rays of both queries), the oracle's BVH2
-itself being checked against brute force over all 2^23 triangles on 512
+itself being checked against brute force over all 2^23 triangles on 4,096
 sampled rays of each query."""
 import numpy as np
 import pytest
@@ -58,7 +58,7 @@ def test_config2_full_size_all_layouts(sc_mod, oracle_mod):
 @pytest.fixture(scope="module")
 def config3(oracle_mod):
     """The 2^23-triangle soup and rays with the oracle's answers for every
-    ray: its BVH2 traversal over all rays, checked on 512 sampled rays of
+    ray: its BVH2 traversal over all rays, checked on 4,096 sampled rays of
     each query against brute force over every triangle (the definition)."""
     sc = scenes.config3_scene()
     assert sc.n_tris == 1 << 23
@@ -70,7 +70,7 @@ def config3(oracle_mod):
     exp = ob.closest(rays)
     eocc = ob.any(short)
     del ob
-    pick = np.sort(np.random.default_rng(5).choice(rays.shape[0], 512, replace=False))
+    pick = np.sort(np.random.default_rng(5).choice(rays.shape[0], 4096, replace=False))
     brute = oracle_mod.closest_brute(tris, rays[pick])
     assert brute.tobytes() == exp[pick].tobytes(), "oracle BVH2 vs brute force (closest)"
     assert np.array_equal(oracle_mod.any_brute(tris, short[pick]), eocc[pick]), "oracle BVH2 vs brute force (any)"
