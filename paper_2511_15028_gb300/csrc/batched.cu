@@ -152,6 +152,8 @@ __global__ void __launch_bounds__(kMaxThreadsPerBlock, kMinBlocksPerSm)
   for (uint32_t i = threadIdx.x; i < cached; i += blockDim.x) starts[i] = scenes[i].begin;
   __syncthreads();
   Stack st;
+  StackTail<false> tail;
+  st.attach(tail);
   st.sh = smem + threadIdx.x;
   st.stride = blockDim.x;
   st.cap_sh = (int)smem_stack;

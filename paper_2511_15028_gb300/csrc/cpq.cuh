@@ -355,6 +355,8 @@ template <bool OWN, int W, int PREC, int SOA, int CREF, bool STATS>
 __device__ __forceinline__ void cpq_kernel_body(const TraceArgs &a) {
   extern __shared__ uint2 smem_stack[];
   Stack st;
+  StackTail<false> tail;
+  st.attach(tail);
   st.sh = smem_stack + threadIdx.x;
   st.stride = blockDim.x;
   st.cap_sh = (int)a.smem_stack;

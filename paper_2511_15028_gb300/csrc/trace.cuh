@@ -284,6 +284,16 @@ __device__ __forceinline__ uint32_t qword(const uint4 (&q)[NQ], int i) {
 // so each index is a compile-time constant and the entries stay in
 // registers); when it is full, a push moves its oldest entry into shared
 // memory. Pops take the register entries first and only then read memory.
+// The local-memory tail of a stack, declared apart from the stack's scalar
+// state: an array indexed at run time lives in local memory, and a struct
+// that held one would take its other members (the stack pointer, the
+// capacity) there with it, costing local loads and stores on every step.
+template <bool TF>
+struct StackTail {
+  uint2 loc[kLocalStack];
+  float locf[TF ? kLocalStack : 1];
+};
+
 template <bool TF, bool RING = false, int R = 0>
 struct StackT {
   uint2 *sh;      // this thread's column in shared memory
@@ -297,9 +307,15 @@ struct StackT {
   uint32_t rr[R > 0 ? R : 1];
   float rt[R > 0 ? R : 1];
   float rf[(R > 0 && TF) ? R : 1];
-  uint2 loc[kLocalStack];
-  float locf[TF ? kLocalStack : 1];
+  uint2 *loc;     // the local-memory tail (StackTail)
+  float *locf;
   static constexpr int kRegs = R;
+  static constexpr bool kTF = TF;
+
+  __device__ __forceinline__ void attach(StackTail<TF> &t) {
+    loc = t.loc;
+    locf = t.locf;
+  }
 
   // Without RING the first cap_sh memory entries live in shared memory and
   // deeper ones in local memory. With RING the shared part holds the cap_sh
@@ -1108,6 +1124,8 @@ template <bool OWN, int W, int PREC, int SOA, int CREF, bool ANY, bool STATS, in
 __device__ __forceinline__ void trace_kernel_body(const TraceArgs &a) {
   extern __shared__ uint2 smem_stack[];
   StackFor<OWN, PREC, W, ANY, REG> st;
+  StackTail<decltype(st)::kTF> tail;
+  st.attach(tail);
   st.sh = smem_stack + threadIdx.x;
   // exit distances (shared-slab layout) follow the entry columns
   st.shf = reinterpret_cast<float *>(smem_stack + blockDim.x * a.smem_stack) + threadIdx.x;
