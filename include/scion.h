@@ -143,8 +143,9 @@ typedef struct {
  *                      values, or a non-zero value for closest point
  *                      queries: SCION_ERR_INVALID_ARG.
  *  smem_stack        : shared-memory stack entries per thread (default 16,
- *                      at most 64; own-box bvh2 layouts other than the shared
- *                      slab round it down to a power of two).
+ *                      at most 64; traces of own-box bvh2 layouts other than
+ *                      the shared slab and of 2/4-wide layouts round it down
+ *                      to a power of two).
  *  ordered_children  : 0 or 1 = children sorted by entry distance
  *                      (closest hit), 2 = stored slot order, 3 = nearest
  *                      child first and the others in slot order.

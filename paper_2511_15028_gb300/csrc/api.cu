@@ -182,13 +182,13 @@ constexpr size_t kSmemOptIn = 32 * 1024;
 // Query kinds of launch_trace.
 constexpr int kQueryClosest = 0, kQueryAny = 1, kQueryPoint = 2;
 
-// Shared-memory stack entries per thread. The own-box bvh2 kernels (all but
-// the shared-slab one) and the any-hit kernels of nodes up to 4 wide keep the
-// shared part of the stack as a ring indexed with a mask, so for them the
-// count is rounded down to a power of two.
+// Shared-memory stack entries per thread. The traversal kernels of the
+// own-box bvh2 nodes (all but the shared-slab one) and of 2/4-wide nodes keep
+// the shared part of the stack as a ring indexed with a mask (StackFor in
+// trace.cuh), so for them the count is rounded down to a power of two.
 uint32_t stack_entries(scion_bvh b, uint32_t requested, int query) {
   const bool ring = query != kQueryPoint && ((b->own_box && b->desc.box_prec != PREC_SLAB) ||
-                                             (!b->own_box && query == kQueryAny && b->desc.width <= 4));
+                                             (!b->own_box && b->desc.width <= 4));
   if (!ring) return requested;
   uint32_t p = 1;
   while (p * 2 <= requested) p *= 2;

@@ -61,9 +61,19 @@ __device__ __forceinline__ void finish_lane(const TraceArgs &a, Lane &L) {
 // (another scene's, or >= total). Not inlined: each family's loops get their
 // own register allocation (inlined into one switch they spill heavily); the
 // call costs once per scene change of a warp.
+// The stack is made here, not passed in: an object whose address crosses a
+// call lives in local memory, and so would the stack pointer on every step.
 template <bool OWN, int W, int PREC, int SOA>
 __device__ __noinline__ unsigned long long run_scene(const BatchScene &S, unsigned long long base,
-                                                     unsigned long long *work, Stack &st) {
+                                                     unsigned long long *work, uint2 *smem_col,
+                                                     uint32_t smem_stack) {
+  Stack st;
+  StackTail<false> tail;
+  st.attach(tail);
+  st.sh = smem_col;
+  st.stride = blockDim.x;
+  st.cap_sh = (int)smem_stack;
+  st.reset();
   const TraceArgs &a = S.a;
   const unsigned long long s_lo = S.begin, s_hi = S.begin + ((a.n + 31ull) & ~31ull);
   const uint32_t lane = threadIdx.x & 31u;
@@ -151,13 +161,7 @@ __global__ void __launch_bounds__(kMaxThreadsPerBlock, kMinBlocksPerSm)
   const uint32_t cached = n_scenes < (uint32_t)kMaxSharedScenes ? n_scenes : (uint32_t)kMaxSharedScenes;
   for (uint32_t i = threadIdx.x; i < cached; i += blockDim.x) starts[i] = scenes[i].begin;
   __syncthreads();
-  Stack st;
-  StackTail<false> tail;
-  st.attach(tail);
-  st.sh = smem + threadIdx.x;
-  st.stride = blockDim.x;
-  st.cap_sh = (int)smem_stack;
-  st.reset();
+  uint2 *const col = smem + threadIdx.x;  // this thread's shared-memory stack column
   unsigned long long base = take_unit(work);
   while (base < total) {
     // last scene whose start <= base (binary search, warp-uniform)
@@ -170,14 +174,14 @@ __global__ void __launch_bounds__(kMaxThreadsPerBlock, kMinBlocksPerSm)
     }
     const BatchScene &S = scenes[lo];
     switch (S.family) {
-      case kFamilyBin: base = run_scene<true, 2, PREC_F32, LAYOUT_AOS>(S, base, work, st); break;
-      case kFamilyBinQ16: base = run_scene<true, 2, PREC_Q16, LAYOUT_AOS>(S, base, work, st); break;
-      case kFamilyW4F32: base = run_scene<false, 4, PREC_F32, LAYOUT_SOA>(S, base, work, st); break;
-      case kFamilyW4F16: base = run_scene<false, 4, PREC_F16, LAYOUT_SOA>(S, base, work, st); break;
-      case kFamilyW4U8: base = run_scene<false, 4, PREC_U8, LAYOUT_SOA>(S, base, work, st); break;
-      case kFamilyW8F16: base = run_scene<false, 8, PREC_F16, LAYOUT_SOA>(S, base, work, st); break;
-      case kFamilyW8U8: base = run_scene<false, 8, PREC_U8, LAYOUT_AOS>(S, base, work, st); break;
-      case kFamilyW8U8S: base = run_scene<false, 8, PREC_U8, LAYOUT_SOA>(S, base, work, st); break;
+      case kFamilyBin: base = run_scene<true, 2, PREC_F32, LAYOUT_AOS>(S, base, work, col, smem_stack); break;
+      case kFamilyBinQ16: base = run_scene<true, 2, PREC_Q16, LAYOUT_AOS>(S, base, work, col, smem_stack); break;
+      case kFamilyW4F32: base = run_scene<false, 4, PREC_F32, LAYOUT_SOA>(S, base, work, col, smem_stack); break;
+      case kFamilyW4F16: base = run_scene<false, 4, PREC_F16, LAYOUT_SOA>(S, base, work, col, smem_stack); break;
+      case kFamilyW4U8: base = run_scene<false, 4, PREC_U8, LAYOUT_SOA>(S, base, work, col, smem_stack); break;
+      case kFamilyW8F16: base = run_scene<false, 8, PREC_F16, LAYOUT_SOA>(S, base, work, col, smem_stack); break;
+      case kFamilyW8U8: base = run_scene<false, 8, PREC_U8, LAYOUT_AOS>(S, base, work, col, smem_stack); break;
+      case kFamilyW8U8S: base = run_scene<false, 8, PREC_U8, LAYOUT_SOA>(S, base, work, col, smem_stack); break;
       default: base = take_unit(work); break;  // batch creation admits only the families above
     }
   }

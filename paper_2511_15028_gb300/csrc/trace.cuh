@@ -735,14 +735,13 @@ __device__ __forceinline__ void step_wide(const TraceArgs &a, Lane &L, S &st, Co
     }
     L.cur = next != kEmptyRef ? next : pop_next<ANY>(st, L.b.t);
   } else {
-    // Nodes up to 4 wide take one triangle per step: the entry then names the
-    // leaf's remaining triangles (first + 1, count - 1), so a lane in a leaf
-    // holds its warp for one triangle test per step rather than for the whole
-    // leaf while the other lanes wait. 8-wide nodes (measured slower that way
-    // on coherent rays) and the counting kernels test the whole leaf at once
-    // (the same triangles, so the same counts).
+    // One triangle per step: the entry then names the leaf's remaining
+    // triangles (first + 1, count - 1), so a lane in a leaf holds its warp for
+    // one triangle test per step rather than for the whole leaf while the
+    // other lanes wait. The counting kernels test the whole leaf at once (the
+    // same triangles, so the same counts).
     const uint32_t count = ref_leaf_count(cur);
-    constexpr bool kWhole = STATS || W > 4;
+    constexpr bool kWhole = STATS;
     if (visit_leaf<ANY, STATS>(a, r, ref_leaf_first(cur), kWhole ? count : 1u, L.b, cnt)) {
       L.found = true;
       L.cur = kEmptyRef;
@@ -950,14 +949,10 @@ __device__ __forceinline__ void start_ray(const TraceArgs &a, Lane &L) {
 }
 
 // The ring pays for its extra register where the kernel has room: the own-box
-// bvh2 kernels (all but the shared slab), the any-hit kernels of nodes up to 4
-// wide and the closest-hit kernels of 2/4-wide nodes with f16 or u8 boxes; in
-// the other 64-register kernels it would spill.
+// bvh2 kernels (all but the shared slab) and the kernels of 2/4-wide nodes; the
+// 8-wide kernels measured slower with it.
 template <bool OWN, int PREC, int W, bool ANY, int REG>
-using StackFor = StackT<OWN && PREC == PREC_SLAB,
-                        (OWN && PREC != PREC_SLAB) ||
-                            (!OWN && W <= 4 && (ANY || PREC == PREC_F16 || PREC == PREC_U8)),
-                        REG>;
+using StackFor = StackT<OWN && PREC == PREC_SLAB, (OWN && PREC != PREC_SLAB) || (!OWN && W <= 4), REG>;
 
 // ------------------------------------------------------------------ kernel body
 // Trace one ray to completion with the layout's step function.

@@ -250,12 +250,12 @@ def test_random_soup_incoherent(sc_mod, oracle_mod):
     ob = oracle_mod.BVH2(tris)
     exp = ob.closest(rays)
     eocc = ob.any(short)
-    for name, d in sc_mod.sweep_layouts(extended=True).items():
+    for name, d in sc_mod.sweep_layouts(extended=True, orders=True).items():
         bvh = sc_mod.scion_build(verts, d)
         for p in (None, dict(rays_per_fetch=1), dict(rays_per_fetch=1, ordered_children=2, threads_per_block=128),
                   dict(ordered_children=3), dict(rays_per_fetch=1, ordered_children=3), dict(rays_per_fetch=8),
                   dict(rays_per_fetch=16, threads_per_block=64), dict(rays_per_fetch=32),
-                  # shallow shared stacks: the own-box kernels' ring spills and refills
+                  # shallow shared stacks: the ring kernels (own-box, 2/4-wide) spill and refill
                   # constantly; 5 and 12 round down to 4 and 8 there
                   dict(smem_stack=1), dict(smem_stack=5, rays_per_fetch=1), dict(smem_stack=12, ordered_children=3),
                   # stack entries in registers, spilling into shallow or default shared parts
