@@ -112,6 +112,13 @@ scion_status scion_debug_build_gpu_host_pack(const float *d_verts, uint64_t n_ve
 scion_status scion_debug_bvh_bytes(scion_bvh bvh, void *nodes, uint64_t nodes_cap, void *nodes2, uint64_t nodes2_cap,
                                    void *prims, uint64_t prims_cap, uint64_t *sizes);
 
+/* Records `device` as the GPU the BVH lives on (test hook; nothing is moved):
+ * with it a test on one GPU can check that calls reject a BVH from another
+ * device with SCION_ERR_INVALID_ARG before anything is issued. The BVH must
+ * be given its real device back before it is traced or destroyed. Touches no
+ * GPU. */
+scion_status scion_debug_set_bvh_device(scion_bvh bvh, int device);
+
 /* Message of the last failing call on the calling host thread (kept per
  * thread; valid until that thread's next failing call). */
 const char *scion_last_error(void);

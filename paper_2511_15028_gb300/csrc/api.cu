@@ -1310,6 +1310,12 @@ scion_status scion_debug_host_decode(scion_host_bvh h, uint32_t *kind, uint32_t 
   return SCION_OK;
 }
 
+scion_status scion_debug_set_bvh_device(scion_bvh b, int device) {
+  if (!b || device < 0) return SCION_ERR_INVALID_ARG;
+  b->device = device;
+  return SCION_OK;
+}
+
 uint64_t scion_debug_raster_slots(uint64_t n, uint32_t raster_width) {
   if (n == 0) return 0;
   TraceArgs a{};

@@ -342,3 +342,32 @@ def test_concurrent_streams_same_bvh_and_host_tracer(sc_mod, oracle_mod):
     assert_same_hits(sc_mod.split_hits(h_o), exp, "host tracer, growing chunks")
     assert np.array_equal(h_a.numpy().astype(np.uint32), eocc)
     assert sc_mod.scion_get_status(bvh) == 0
+
+
+def test_bvh_from_another_device_is_rejected(sc_mod):
+    """Every call that takes a BVH checks that it lives on the current device:
+    a BVH recorded as another GPU's is rejected with INVALID_ARG before
+    anything is issued, and works again once its own device is restored."""
+    L = sc_mod.lib()
+    L.scion_debug_set_bvh_device.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.scion_debug_set_bvh_device.restype = ctypes.c_int
+    sc = scenes.config1_scene()
+    bvh = sc_mod.scion_build(sc.verts, sc_mod.layout(width=4, box_layout="soa"), sc.indices)
+    rays = torch.from_numpy(scenes.config1_rays()[:256]).cuda()
+    pts = torch.tensor([[0.1, 0.2, 0.5, float("inf")]], device="cuda")
+    dv = torch.from_numpy(sc.verts).cuda()
+    dev = torch.cuda.current_device()
+    expected = sc_mod.scion_trace_closest(bvh, rays).clone()
+    assert L.scion_debug_set_bvh_device(bvh.handle, dev + 1) == 0
+    try:
+        calls = (lambda: sc_mod.scion_trace_closest(bvh, rays), lambda: sc_mod.scion_trace_any(bvh, rays),
+                 lambda: sc_mod.scion_query_closest_point(bvh, pts), lambda: sc_mod.scion_refit(bvh, dv))
+        for call in calls:
+            with pytest.raises(sc_mod.ScionError) as e:
+                call()
+            assert e.value.status == 1 and "built on device" in str(e.value), str(e.value)
+    finally:
+        assert L.scion_debug_set_bvh_device(bvh.handle, dev) == 0
+    got = sc_mod.scion_trace_closest(bvh, rays)
+    torch.cuda.synchronize()
+    assert torch.equal(got, expected)
