@@ -1039,8 +1039,9 @@ def main():
                 "frac_of_measured_hbm": round(achieved / hbm_peak, 4), "hbm_peak": hbm_peak,
                 "hbm_peak_source": peak_src,
                 "note": "algorithmic bytes = rays x 48 + nodes visited x node bytes + triangles tested x "
-                        "triangle bytes (counting kernel) over the launches' CUDA-event durations; the BVH "
-                        "fits in L2, so the roof is the L2 read bandwidth and DRAM traffic (traffic) is small"}
+                        "triangle bytes (counting kernel) of one primary and one bounce launch over their "
+                        "CUDA-event durations; the BVH fits in L2, so the roof is the L2 read bandwidth; "
+                        "traffic / l2_traffic = ncu DRAM / L2 bytes of the same two launches (cold caches)"}
     emit(rank, {"section": "coherent_layouts", "workload": WORKLOAD, "best": best,
                 "pareto": pareto({k: (v["bvh_mb"], v["mrays_s"]) for k, v in results.items()}),
                 "layouts": {k: {kk: vv for kk, vv in v.items() if kk not in ("alg_bytes", "_bvh")}
