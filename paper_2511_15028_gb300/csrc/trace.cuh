@@ -110,7 +110,10 @@ __device__ __forceinline__ void setup_ray(const float4 a, const float4 b, Ray &r
   r.kx = kx; r.ky = ky; r.kz = kz;
   r.Sx = __fdiv_rn(sel3(r.dx, r.dy, r.dz, kx), dkz);
   r.Sy = __fdiv_rn(sel3(r.dx, r.dy, r.dz, ky), dkz);
-  r.Sz = __fdiv_rn(1.0f, dkz);
+  // 1 / d[kz] is the slab reciprocal of that axis already (the same IEEE
+  // division: safe_rcp replaces only a zero component, and d[kz] = 0 only when
+  // every component is 0, where 1 / +-0 = +-inf)
+  r.Sz = dkz != 0.0f ? sel3(r.rx, r.ry, r.rz, kz) : copysignf(__int_as_float(0x7f800000), dkz);
 }
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
